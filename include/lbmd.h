@@ -1,0 +1,188 @@
+/*
+ * lbmd.h -- C ABI of the GB300 (sm_103a) coupled lattice-Boltzmann /
+ * molecular-dynamics step.
+ *
+ * Method: Lauricella et al., "Multiscale Hybrid Modeling of Proteins in
+ * Solvent" (arXiv 2305.05025), Sec. 2.2. One coupled step:
+ *   1. the fluid velocity u = (sum_i f_i c_i + g/2)/rho (Eq. 2, Guo half-shift
+ *      of the body force g) is interpolated trilinearly at every atom from the
+ *      eight nearest nodes;
+ *   2. the atoms advance by n_md velocity-Verlet substeps of 1/n_md under
+ *      shifted-force Lennard-Jones + harmonic bonds and the Stokes friction
+ *      gamma (U - v), U held fixed over the step;
+ *   3. the opposite of each atom's friction impulse is spread back onto the
+ *      same eight nodes with the same weights;
+ *   4. every node is collided with the BGK operator -omega (f - f_eq) and the
+ *      Guo source of the total force g + G (Eq. 1), omega = 1/tau,
+ *      nu = (tau - 1/2)/3, and streamed.
+ * Lattice units throughout: Delta x = Delta t = 1, c_s^2 = 1/3.
+ *
+ * Conventions
+ *  - Node (x, y, z), 0 <= x < nx ..., has linear index (z*ny + y)*nx + x.
+ *  - D3Q19 speeds in this order: 0 rest; 1..6 = +x -x +y -y +z -z;
+ *    7..18 = (1,1,0) (-1,-1,0) (1,-1,0) (-1,1,0) (1,0,1) (-1,0,-1) (1,0,-1)
+ *    (-1,0,1) (0,1,1) (0,-1,-1) (0,1,-1) (0,-1,1). Speed 2k-1 and 2k are
+ *    opposite.
+ *  - Populations cross the ABI as structure-of-arrays, population i of node
+ *    n at [i*N + n], N = nx*ny*nz, in FP32: the post-streaming distribution
+ *    f_i(r, t) of Eq. (1), whatever the internal storage format.
+ *  - Atom arrays are SoA: component d of atom a at [d*n_atoms + a].
+ *    Positions are FP64 and unwrapped (periodic images are taken by the
+ *    library); velocities FP32.
+ *  - The caller owns every buffer it passes. The library copies on entry and
+ *    exit and never keeps a caller pointer.
+ *  - on_device = 1: the pointers are CUDA device pointers; 0: host pointers.
+ *  - All device work is enqueued on the stream given to lbmd_create, so calls
+ *    are ordered with the caller's other work on that stream. Calls that
+ *    return data to the host synchronise that stream.
+ *  - Every call returns a status and never aborts; lbmd_last_error gives the
+ *    message. No kernel of the library traps or waits on a flag.
+ *  - A handle is not thread safe: one thread at a time.
+ */
+#ifndef LBMD_H
+#define LBMD_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lbmd_s *lbmd_t;
+
+typedef enum {
+    LBMD_OK = 0,
+    LBMD_ERR_ARG = 1,       /* invalid argument or parameter combination */
+    LBMD_ERR_ALLOC = 2,     /* device or host allocation failed */
+    LBMD_ERR_CUDA = 3,      /* a CUDA runtime call failed (message has the CUDA error) */
+    LBMD_ERR_NONFINITE = 4, /* a NaN or Inf appeared in the lattice or the atoms */
+    LBMD_ERR_CELL = 5,      /* a pair-search cell held more atoms than its capacity:
+                               that step's forces miss pairs */
+    LBMD_ERR_STATE = 6      /* call out of order (no state set), or an atom's
+                               interpolation stencil crossed a z wall */
+} lbmd_status;
+
+/* Storage format of the populations. All arithmetic is FP32; the shifted
+ * formats store delta f_i = f_i - w_i rho0 (halving the bytes per node). */
+enum { LBMD_F32 = 0, LBMD_F16_SHIFTED = 1, LBMD_BF16_SHIFTED = 2 };
+
+/* Body force g(x) (not in the paper; the workloads' driving). */
+enum {
+    LBMD_FORCE_NONE = 0,
+    LBMD_FORCE_UNIFORM = 1,    /* g = A e_dir */
+    LBMD_FORCE_KOLMOGOROV = 2, /* g = A sin(2 pi x_axis / n_axis) e_dir */
+    LBMD_FORCE_POISEUILLE = 3  /* g = A e_dir, meant with walls_z = 1 */
+};
+
+/* Observables of lbmd_backward. */
+enum {
+    LBMD_OBS_DRAG_X = 0, /* (1/T) sum_steps sum_atoms J_x: mean friction force the
+                            fluid exerts on the solute along x */
+    LBMD_OBS_RG2 = 1     /* (1/T) sum_steps R_g^2 after each step (mass weighted) */
+};
+
+typedef struct {
+    int nx, ny, nz;           /* lattice nodes per axis (>= 1; >= 2 along z with walls) */
+    double tau;               /* BGK relaxation time, > 1/2 (omega = 1/tau) */
+    double rho0;              /* reference density (shift of the stored populations) */
+    double gamma;             /* Stokes friction coefficient, force = gamma (U - v) */
+    double dt;                /* coupled time step in lattice units: must be 1 */
+    int n_md;                 /* velocity-Verlet substeps per coupled step, >= 1 */
+    double lj_eps, lj_sigma;  /* Lennard-Jones well depth and diameter */
+    double lj_rcut_over_sigma;/* cutoff radius in units of sigma */
+    double skin;              /* extra cell side beyond the cutoff (>= 0) */
+    int forcing;              /* LBMD_FORCE_* */
+    double force_amp;         /* A */
+    int force_dir;            /* component of g (0, 1, 2) */
+    int force_wave_axis;      /* axis of the Kolmogorov wave (0, 1, 2) */
+    int walls_z;              /* 1: half-way bounce-back walls at z = -1/2, nz - 1/2 */
+    int store;                /* LBMD_F32, LBMD_F16_SHIFTED, LBMD_BF16_SHIFTED */
+    int deterministic;        /* reserved, must be 0 */
+    int check_every;          /* lbmd_step polls the device error flags every this
+                                 many steps (0: only lbmd_check / lbmd_get_stats do) */
+} lbmd_params;
+
+/* Creates a handle: validates the parameters (LBMD_ERR_ARG before any device
+ * work), allocates the lattice (two population buffers of N*19 elements of
+ * the storage format), the atom arrays and the pair-search cells, and uploads
+ * the topology. mass: n_atoms masses (> 0). bonds: 2*n_bonds atom indices;
+ * bond_k, bond_r0: n_bonds stiffnesses and rest lengths (U = k (r - r0)^2/2).
+ * Bonded pairs are excluded from the Lennard-Jones sum. n_atoms may be 0 (a
+ * lattice-only run). cuda_stream: a cudaStream_t (NULL: the legacy default
+ * stream). Host pointers. On failure *out is NULL. */
+lbmd_status lbmd_create(const lbmd_params *params, int n_atoms, const double *mass, int n_bonds,
+                        const int32_t *bonds, const double *bond_k, const double *bond_r0,
+                        void *cuda_stream, lbmd_t *out);
+
+/* Sets the state. f: FP32 post-streaming populations (19*N SoA); or, when f
+ * is NULL, rho (N) and u (3*N SoA) give f = f_eq(rho, u) (the second-order
+ * equilibrium of Sec. 2.2). x (FP64) and v (FP32): 3*n_atoms SoA, required
+ * when n_atoms > 0. Also computes the conservative forces at x and fills
+ * the pair-search cells. Resets the step counter to 0. */
+lbmd_status lbmd_set_state(lbmd_t h, const float *f, const float *rho, const float *u,
+                           const double *x, const float *v, int on_device);
+
+/* Advances n_steps coupled steps (asynchronous; each step is one CUDA graph
+ * launch). Returns LBMD_ERR_STATE if no state was set. Polls the device flags
+ * only when check_every > 0 and a multiple of it is crossed. */
+lbmd_status lbmd_step(lbmd_t h, int n_steps);
+
+/* Copies out the current state; any pointer may be NULL. f: FP32
+ * post-streaming populations (19*N); rho (N); u (3*N), the velocity
+ * (sum f c + g/2)/rho; x (3*n_atoms FP64); v (3*n_atoms FP32). Synchronises
+ * the stream when on_device = 0. */
+lbmd_status lbmd_get_fields(lbmd_t h, float *f, float *rho, float *u, double *x, float *v,
+                            int on_device);
+
+/* FP64 global sums: fluid mass sum_x sum_i f_i, fluid momentum
+ * sum_x sum_i f_i c_i, solute momentum sum_a m_a v_a (host outputs, any may be
+ * NULL). Synchronises; returns LBMD_ERR_NONFINITE if a NaN/Inf was found. */
+lbmd_status lbmd_get_stats(lbmd_t h, double *mass, double mom_fluid[3], double mom_atoms[3]);
+
+/* Synchronises and returns the first raised device flag as a status
+ * (NONFINITE, CELL, STATE), clearing the flags. */
+lbmd_status lbmd_check(lbmd_t h);
+
+/* Pair-search diagnostics at the current positions: cell_of[a] = linear
+ * index (cz*ncy + cy)*ncx + cx of atom a's cell, cx = floor(x*ncx/nx) mod ncx
+ * in FP64, ncx = floor(nx/(rcut + skin)); neighbours[a] = number of other
+ * atoms with r^2 < rcut^2 (FP64, minimum image). nc (3 ints, host) receives
+ * the cell grid. Any output may be NULL. */
+lbmd_status lbmd_cell_list(lbmd_t h, int32_t *cell_of, int32_t *neighbours, int32_t *nc,
+                           int on_device);
+
+/* Changes gamma, tau and the body-force amplitude of an existing handle
+ * (the step graph is rebuilt on the next lbmd_step). */
+lbmd_status lbmd_set_physics(lbmd_t h, double gamma, double tau, double force_amp);
+
+/* Routes the start/stop of the lattice kernel of the NEXT step launch to two
+ * caller events (cudaEvent_t, created with timing enabled), so the caller can
+ * time that kernel with cudaEventElapsedTime on the stream it runs on.
+ * NULL, NULL restores the library's own events. */
+lbmd_status lbmd_set_timing_events(lbmd_t h, void *ev_start, void *ev_stop);
+
+/* Differentiable rollout (not in the paper: the adjoint of the coupled step).
+ * Runs n_steps steps from the current state, keeping a checkpoint every
+ * ckpt_every steps, evaluates the observable (LBMD_OBS_*) and, by the
+ * discrete adjoint (reverse collide-stream, reverse interpolate/spread,
+ * reverse velocity Verlet), its derivatives with respect to gamma, tau and
+ * force_amp. Outputs are host doubles (any may be NULL). The state ends
+ * advanced by n_steps, as after lbmd_step(n_steps). */
+lbmd_status lbmd_backward(lbmd_t h, int n_steps, int ckpt_every, int observable, double *d_gamma,
+                          double *d_tau, double *d_force_amp, double *obs);
+
+/* Message of the last failed call on this handle (or of the last failed
+ * lbmd_create on this thread when h is NULL). Never NULL. */
+const char *lbmd_last_error(lbmd_t h);
+
+/* Frees every resource of the handle (synchronises its stream). NULL is a no-op. */
+void lbmd_destroy(lbmd_t h);
+
+/* ABI version, currently 1. */
+int lbmd_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LBMD_H */

@@ -1,0 +1,632 @@
+// C ABI of the coupled LB-MD step (declared in include/lbmd.h): handle
+// lifetime, parameter validation, device memory, the per-step CUDA graph and
+// the state/diagnostic calls.
+//
+// One coupled step is one graph launch with two branches:
+//   lattice branch (low priority):  dense stream-collide of every node (g only)
+//   solute branch (high priority):  interpolate + claim -> n_md+1 substep
+//                                   kernels -> spread
+// joined by the sparse fix-up of the claimed nodes (g + G), whose last block
+// advances the device step counter. The dense lattice pass does not depend on
+// the solute, so the two branches overlap.
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "lbmd_internal.cuh"
+
+using namespace lbmd;
+
+namespace {
+
+thread_local std::string g_create_error;
+
+constexpr int kFold = 64;  // bucket grid per axis (cells folded modulo this)
+constexpr int kCap = 64;   // atoms per bucket
+
+}  // namespace
+
+struct lbmd_s {
+    lbmd_params p{};
+    cudaStream_t stream = nullptr;            // caller's stream
+    cudaStream_t s_main = nullptr, s_lat = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_t0 = nullptr, ev_t1 = nullptr;
+    int na = 0, nb = 0;
+    Lat L{};
+    AtomArgs A{};
+    CouplingArgs C{};
+    void *pop[2] = {nullptr, nullptr};
+    DevState *ds = nullptr;
+    double *red = nullptr;  // partials
+    double *red_out = nullptr;
+    int red_blocks = 0;
+    int fix_grid = 1;
+    std::vector<void *> allocs;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    cudaGraphNode_t node_t0 = nullptr, node_t1 = nullptr;
+    bool state_set = false;
+    long long steps = 0;
+    std::string err;
+    int alloc_count = 0;
+    void *stage = nullptr;  // device staging for host-pointer set/get (lazily sized)
+    size_t stage_bytes = 0;
+};
+
+namespace {
+
+lbmd_status fail(lbmd_t h, lbmd_status s, const std::string &msg) {
+    if (h)
+        h->err = msg;
+    else
+        g_create_error = msg;
+    return s;
+}
+
+lbmd_status cuda_fail(lbmd_t h, cudaError_t e, const char *what) {
+    return fail(h, e == cudaErrorMemoryAllocation ? LBMD_ERR_ALLOC : LBMD_ERR_CUDA,
+                std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define CK(h, call)                                                                                                 \
+    do {                                                                                                            \
+        cudaError_t e_ = (call);                                                                                    \
+        if (e_ != cudaSuccess) return cuda_fail((h), e_, #call);                                                    \
+    } while (0)
+
+// Device allocation with a test hook: LBMD_TEST_FAIL_ALLOC=k makes the k-th
+// allocation of a handle report failure (host-side fault injection).
+lbmd_status dalloc(lbmd_t h, void **ptr, size_t bytes) {
+    *ptr = nullptr;
+    ++h->alloc_count;
+    if (const char *env = std::getenv("LBMD_TEST_FAIL_ALLOC")) {
+        if (std::atoi(env) == h->alloc_count)
+            return fail(h, LBMD_ERR_ALLOC, "simulated allocation failure (LBMD_TEST_FAIL_ALLOC)");
+    }
+    cudaError_t e = cudaMalloc(ptr, bytes < 16 ? 16 : bytes);
+    if (e != cudaSuccess) {
+        *ptr = nullptr;
+        return cuda_fail(h, e, "cudaMalloc");
+    }
+    h->allocs.push_back(*ptr);
+    return LBMD_OK;
+}
+
+template <class T> lbmd_status dalloc_t(lbmd_t h, T **ptr, size_t count) {
+    void *p = nullptr;
+    lbmd_status s = dalloc(h, &p, count * sizeof(T));
+    *ptr = (T *)p;
+    return s;
+}
+
+#define TRY(expr)                                                                                                   \
+    do {                                                                                                            \
+        lbmd_status s_ = (expr);                                                                                    \
+        if (s_ != LBMD_OK) return s_;                                                                               \
+    } while (0)
+
+std::string validate(const lbmd_params *p, int n_atoms, const double *mass, int n_bonds, const int32_t *bonds,
+                     const double *bond_k, const double *bond_r0) {
+    if (!p) return "params is NULL";
+    if (p->nx < 1 || p->ny < 1 || p->nz < 1) return "lattice sizes must be >= 1";
+    const double N = (double)p->nx * p->ny * p->nz;
+    if (N >= 2147483647.0) return "nx*ny*nz must be < 2^31";
+    if (!(p->tau > 0.5)) return "tau must be > 1/2 (positive viscosity)";
+    if (!(p->rho0 > 0)) return "rho0 must be > 0";
+    if (!(p->dt == 1.0)) return "dt must be 1 (lattice units: one LB time unit per coupled step)";
+    if (!(p->gamma >= 0)) return "gamma must be >= 0";
+    if (p->store < 0 || p->store > 2) return "store must be LBMD_F32, LBMD_F16_SHIFTED or LBMD_BF16_SHIFTED";
+    if (p->forcing < 0 || p->forcing > 3) return "unknown forcing";
+    if (p->force_dir < 0 || p->force_dir > 2 || p->force_wave_axis < 0 || p->force_wave_axis > 2)
+        return "force_dir and force_wave_axis must be 0, 1 or 2";
+    if (!std::isfinite(p->force_amp)) return "force_amp must be finite";
+    if (p->walls_z != 0 && p->walls_z != 1) return "walls_z must be 0 or 1";
+    if (p->walls_z && p->nz < 2) return "walls_z needs nz >= 2";
+    if (p->deterministic != 0) return "deterministic mode is not available";
+    if (p->check_every < 0) return "check_every must be >= 0";
+    if (n_atoms < 0) return "n_atoms must be >= 0";
+    if (n_bonds < 0) return "n_bonds must be >= 0";
+    if (n_atoms > 0) {
+        if (!mass) return "mass is NULL";
+        for (int a = 0; a < n_atoms; ++a)
+            if (!(mass[a] > 0) || !std::isfinite(mass[a])) return "masses must be positive and finite";
+        if (p->n_md < 1) return "n_md must be >= 1";
+        if (!(p->lj_sigma > 0) || !(p->lj_rcut_over_sigma > 0) || !(p->lj_eps >= 0)) return "invalid LJ parameters";
+        if (!(p->skin >= 0)) return "skin must be >= 0";
+        const double rc = p->lj_sigma * p->lj_rcut_over_sigma;
+        const double side = rc + p->skin;
+        const int L[3] = {p->nx, p->ny, p->nz};
+        for (int d = 0; d < 3; ++d) {
+            const int nc = (int)std::floor((double)L[d] / side);
+            if (nc < 3) return "each box side must hold at least 3 pair-search cells (side >= 3 (rcut + skin))";
+            if (nc > 1023) return "at most 1023 pair-search cells per axis";
+        }
+    }
+    if (n_bonds > 0) {
+        if (!bonds || !bond_k || !bond_r0) return "bond arrays are NULL";
+        for (int b = 0; b < n_bonds; ++b) {
+            const int i = bonds[2 * b], j = bonds[2 * b + 1];
+            if (i < 0 || j < 0 || i >= n_atoms || j >= n_atoms || i == j) return "bond index out of range";
+            if (!std::isfinite(bond_k[b]) || !std::isfinite(bond_r0[b]) || bond_r0[b] < 0) return "invalid bond";
+        }
+    }
+    return "";
+}
+
+void fill_physics(lbmd_t h) {
+    const lbmd_params &p = h->p;
+    Lat &L = h->L;
+    L.nx = p.nx;
+    L.ny = p.ny;
+    L.nz = p.nz;
+    L.N = (size_t)p.nx * p.ny * p.nz;
+    L.omega = (float)(1.0 / p.tau);
+    L.rho0 = (float)p.rho0;
+    L.walls = p.walls_z;
+    L.forcing = p.forcing;
+    L.famp = (float)p.force_amp;
+    L.fdir = p.force_dir;
+    L.faxis = p.force_wave_axis;
+    const int nax = p.force_wave_axis == 0 ? p.nx : (p.force_wave_axis == 1 ? p.ny : p.nz);
+    L.kwave = (float)(2.0 / nax);
+
+    AtomArgs &A = h->A;
+    A.na = h->na;
+    A.n_md = p.n_md > 0 ? p.n_md : 1;
+    A.dt = (float)(1.0 / A.n_md);
+    A.hdt = (float)(0.5 / A.n_md);
+    A.gamma = (float)p.gamma;
+    const double rc = p.lj_sigma * p.lj_rcut_over_sigma;
+    A.lj_sig2 = (float)(p.lj_sigma * p.lj_sigma);
+    A.lj_24eps = (float)(24.0 * p.lj_eps);
+    const double sr6 = std::pow(p.lj_sigma / rc, 6.0);
+    A.lj_fc = (float)(24.0 * p.lj_eps * (2.0 * sr6 * sr6 - sr6) / rc);
+    A.rc2f = (float)(rc * rc);
+    A.rc2d = rc * rc;
+    const int Ls[3] = {p.nx, p.ny, p.nz};
+    for (int d = 0; d < 3; ++d) {
+        A.nc[d] = h->na > 0 ? (int)std::floor((double)Ls[d] / (rc + p.skin)) : 3;
+        A.fold[d] = A.nc[d] < kFold ? A.nc[d] : kFold;
+        A.Ld[d] = (double)Ls[d];
+        A.hd[d] = (double)Ls[d] / A.nc[d];
+        A.h[d] = (float)A.hd[d];
+        A.inv_h[d] = (float)(A.nc[d] / (double)Ls[d]);
+    }
+    A.cap = kCap;
+    h->C.L = L;
+    h->C.na = h->na;
+}
+
+void destroy_graph(lbmd_t h) {
+    if (h->exec) cudaGraphExecDestroy(h->exec);
+    if (h->graph) cudaGraphDestroy(h->graph);
+    h->exec = nullptr;
+    h->graph = nullptr;
+    h->node_t0 = h->node_t1 = nullptr;
+}
+
+lbmd_status enqueue_step(lbmd_t h) {
+    // Lattice branch.
+    CK(h, cudaEventRecord(h->ev_fork, h->s_main));
+    CK(h, cudaStreamWaitEvent(h->s_lat, h->ev_fork, 0));
+    CK(h, cudaEventRecordWithFlags(h->ev_t0, h->s_lat, cudaEventRecordExternal));
+    CK(h, launch_lb_step(h->p.store, h->L, h->pop, h->ds, h->s_lat));
+    CK(h, cudaEventRecordWithFlags(h->ev_t1, h->s_lat, cudaEventRecordExternal));
+    CK(h, cudaEventRecord(h->ev_join, h->s_lat));
+    // Solute branch.
+    if (h->na > 0) {
+        CK(h, launch_interp(h->p.store, h->C, h->A, h->pop, h->s_main));
+        for (int k = 0; k <= h->A.n_md; ++k) CK(h, launch_md_substep(h->A, k, h->s_main));
+        CK(h, launch_spread(h->C, h->s_main));
+    }
+    CK(h, cudaStreamWaitEvent(h->s_main, h->ev_join, 0));
+    CK(h, launch_lb_fix(h->p.store, h->L, h->pop, h->C, h->fix_grid, h->s_main));
+    return LBMD_OK;
+}
+
+lbmd_status build_graph(lbmd_t h) {
+    destroy_graph(h);
+    CK(h, cudaStreamBeginCapture(h->s_main, cudaStreamCaptureModeThreadLocal));
+    lbmd_status s = enqueue_step(h);
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamEndCapture(h->s_main, &g);
+    if (s != LBMD_OK) {
+        if (g) cudaGraphDestroy(g);
+        return s;
+    }
+    if (e != cudaSuccess) return cuda_fail(h, e, "cudaStreamEndCapture");
+    h->graph = g;
+    CK(h, cudaGraphInstantiate(&h->exec, h->graph, 0));
+    size_t n = 0;
+    CK(h, cudaGraphGetNodes(h->graph, nullptr, &n));
+    std::vector<cudaGraphNode_t> nodes(n);
+    CK(h, cudaGraphGetNodes(h->graph, nodes.data(), &n));
+    for (auto nd : nodes) {
+        cudaGraphNodeType t;
+        CK(h, cudaGraphNodeGetType(nd, &t));
+        if (t != cudaGraphNodeTypeEventRecord) continue;
+        cudaEvent_t ev = nullptr;
+        CK(h, cudaGraphEventRecordNodeGetEvent(nd, &ev));
+        if (ev == h->ev_t0) h->node_t0 = nd;
+        if (ev == h->ev_t1) h->node_t1 = nd;
+    }
+    return LBMD_OK;
+}
+
+lbmd_status read_flags(lbmd_t h) {
+    int flags = 0;
+    CK(h, cudaMemcpyAsync(&flags, &h->ds->flags, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    CK(h, cudaStreamSynchronize(h->stream));
+    if (!flags) return LBMD_OK;
+    const int zero = 0;
+    CK(h, cudaMemcpyAsync(&h->ds->flags, &zero, sizeof(int), cudaMemcpyHostToDevice, h->stream));
+    CK(h, cudaStreamSynchronize(h->stream));
+    if (flags & FLAG_NONFINITE) return fail(h, LBMD_ERR_NONFINITE, "non-finite value in the lattice or the atoms");
+    if (flags & FLAG_CELL)
+        return fail(h, LBMD_ERR_CELL, "a pair-search bucket overflowed: forces of a step missed pairs");
+    if (flags & FLAG_WALL) return fail(h, LBMD_ERR_STATE, "an atom's interpolation stencil crossed a z wall");
+    return fail(h, LBMD_ERR_STATE, "touched-node list overflowed");
+}
+
+// Copies n bytes from a caller buffer into device memory (staging helper).
+lbmd_status to_device(lbmd_t h, void *dst, const void *src, size_t n, int on_device) {
+    CK(h, cudaMemcpyAsync(dst, src, n, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, h->stream));
+    return LBMD_OK;
+}
+
+// Device staging area for calls with host pointers, grown on demand and kept
+// for the handle's lifetime (so repeated host-pointer calls allocate nothing).
+cudaError_t stage(lbmd_t h, size_t bytes, void **out) {
+    if (h->stage_bytes < bytes) {
+        if (h->stage) {
+            cudaStreamSynchronize(h->stream);
+            cudaFree(h->stage);
+            h->stage = nullptr;
+            h->stage_bytes = 0;
+        }
+        cudaError_t e = cudaMalloc(&h->stage, bytes);
+        if (e != cudaSuccess) return e;
+        h->stage_bytes = bytes;
+    }
+    *out = h->stage;
+    return cudaSuccess;
+}
+
+}  // namespace
+
+extern "C" {
+
+int lbmd_version(void) { return 1; }
+
+const char *lbmd_last_error(lbmd_t h) { return h ? h->err.c_str() : g_create_error.c_str(); }
+
+lbmd_status lbmd_create(const lbmd_params *params, int n_atoms, const double *mass, int n_bonds,
+                        const int32_t *bonds, const double *bond_k, const double *bond_r0, void *cuda_stream,
+                        lbmd_t *out) {
+    if (!out) return fail(nullptr, LBMD_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    std::string why = validate(params, n_atoms, mass, n_bonds, bonds, bond_k, bond_r0);
+    if (!why.empty()) return fail(nullptr, LBMD_ERR_ARG, why);
+
+    lbmd_t h = new (std::nothrow) lbmd_s();
+    if (!h) return fail(nullptr, LBMD_ERR_ALLOC, "host allocation failed");
+    h->p = *params;
+    h->stream = (cudaStream_t)cuda_stream;
+    h->na = n_atoms;
+    h->nb = n_bonds;
+    fill_physics(h);
+
+    auto bail = [&](lbmd_status s) {
+        g_create_error = h->err;
+        lbmd_destroy(h);
+        return s;
+    };
+#define CREATE_TRY(expr)                                                                                            \
+    do {                                                                                                            \
+        lbmd_status s_ = (expr);                                                                                    \
+        if (s_ != LBMD_OK) return bail(s_);                                                                         \
+    } while (0)
+#define CREATE_CK(call)                                                                                             \
+    do {                                                                                                            \
+        cudaError_t e_ = (call);                                                                                    \
+        if (e_ != cudaSuccess) return bail(cuda_fail(h, e_, #call));                                                \
+    } while (0)
+
+    int lo = 0, hi = 0;
+    CREATE_CK(cudaDeviceGetStreamPriorityRange(&lo, &hi));
+    CREATE_CK(cudaStreamCreateWithPriority(&h->s_main, cudaStreamNonBlocking, hi));
+    CREATE_CK(cudaStreamCreateWithPriority(&h->s_lat, cudaStreamNonBlocking, lo));
+    CREATE_CK(cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming));
+    CREATE_CK(cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming));
+    CREATE_CK(cudaEventCreate(&h->ev_t0));
+    CREATE_CK(cudaEventCreate(&h->ev_t1));
+
+    const Lat &L = h->L;
+    const size_t pop_bytes = L.N * Q * store_bytes(h->p.store);
+    CREATE_TRY(dalloc(h, &h->pop[0], pop_bytes));
+    CREATE_TRY(dalloc(h, &h->pop[1], pop_bytes));
+    CREATE_TRY(dalloc_t(h, &h->ds, 1));
+    CREATE_TRY(dalloc_t(h, &h->C.G, L.N));
+    CREATE_TRY(dalloc_t(h, &h->C.tag, L.N));
+    h->red_blocks = (int)std::min<size_t>((L.N + 255) / 256, 1024);
+    CREATE_TRY(dalloc_t(h, &h->red, (size_t)h->red_blocks * 4));
+    CREATE_TRY(dalloc_t(h, &h->red_out, 8));
+    CREATE_CK(cudaMemsetAsync(h->C.G, 0, L.N * sizeof(float4), h->stream));
+    CREATE_CK(cudaMemsetAsync(h->C.tag, 0, L.N * sizeof(int), h->stream));
+    CREATE_CK(cudaMemsetAsync(h->ds, 0, sizeof(DevState), h->stream));
+
+    AtomArgs &A = h->A;
+    CouplingArgs &C = h->C;
+    A.ds = C.ds = h->ds;
+    const int na = h->na;
+    const size_t na3 = (size_t)3 * (na > 0 ? na : 1);
+    if (na > 0) {
+        CREATE_TRY(dalloc_t(h, &A.X, na3));
+        CREATE_TRY(dalloc_t(h, &A.P[0], (size_t)na));
+        CREATE_TRY(dalloc_t(h, &A.P[1], (size_t)na));
+        CREATE_TRY(dalloc_t(h, &A.P0, na3));
+        CREATE_TRY(dalloc_t(h, &A.Plo, na3));
+        CREATE_TRY(dalloc_t(h, &A.V, na3));
+        CREATE_TRY(dalloc_t(h, &A.F, na3));
+        CREATE_TRY(dalloc_t(h, &A.U, na3));
+        CREATE_TRY(dalloc_t(h, &A.J, na3));
+        CREATE_TRY(dalloc_t(h, &A.mass, (size_t)na));
+        CREATE_TRY(dalloc_t(h, &A.inv_m, (size_t)na));
+        CREATE_TRY(dalloc_t(h, &C.base, na3));
+        CREATE_TRY(dalloc_t(h, &C.frac, na3));
+        C.touched_cap = 8 * na;
+        CREATE_TRY(dalloc_t(h, &C.touched, (size_t)C.touched_cap));
+        const size_t B = (size_t)A.fold[0] * A.fold[1] * A.fold[2];
+        for (int g = 0; g < 3; ++g) {
+            CREATE_TRY(dalloc_t(h, &A.count[g], B));
+            CREATE_TRY(dalloc_t(h, &A.slot[g], B * A.cap));
+            CREATE_TRY(dalloc_t(h, &A.bucket[g], (size_t)na));
+        }
+        // Topology: masses and a symmetric bond CSR.
+        std::vector<float> m(na), im(na);
+        for (int a = 0; a < na; ++a) {
+            m[a] = (float)mass[a];
+            im[a] = (float)(1.0 / mass[a]);
+        }
+        std::vector<int> start(na + 1, 0), part(2 * (size_t)n_bonds + 1), fill(na, 0);
+        std::vector<float> bk(2 * (size_t)n_bonds + 1), br0(2 * (size_t)n_bonds + 1);
+        for (int b = 0; b < n_bonds; ++b) {
+            start[bonds[2 * b] + 1]++;
+            start[bonds[2 * b + 1] + 1]++;
+        }
+        for (int a = 0; a < na; ++a) start[a + 1] += start[a];
+        for (int b = 0; b < n_bonds; ++b) {
+            const int i = bonds[2 * b], j = bonds[2 * b + 1];
+            const int si = start[i] + fill[i]++, sj = start[j] + fill[j]++;
+            part[si] = j;
+            part[sj] = i;
+            bk[si] = bk[sj] = (float)bond_k[b];
+            br0[si] = br0[sj] = (float)bond_r0[b];
+        }
+        int *d_start, *d_part;
+        float *d_bk, *d_br0;
+        CREATE_TRY(dalloc_t(h, &d_start, (size_t)na + 1));
+        CREATE_TRY(dalloc_t(h, &d_part, part.size()));
+        CREATE_TRY(dalloc_t(h, &d_bk, bk.size()));
+        CREATE_TRY(dalloc_t(h, &d_br0, br0.size()));
+        CREATE_CK(cudaMemcpy(d_start, start.data(), start.size() * sizeof(int), cudaMemcpyHostToDevice));
+        CREATE_CK(cudaMemcpy(d_part, part.data(), part.size() * sizeof(int), cudaMemcpyHostToDevice));
+        CREATE_CK(cudaMemcpy(d_bk, bk.data(), bk.size() * sizeof(float), cudaMemcpyHostToDevice));
+        CREATE_CK(cudaMemcpy(d_br0, br0.data(), br0.size() * sizeof(float), cudaMemcpyHostToDevice));
+        CREATE_CK(cudaMemcpy(A.mass, m.data(), na * sizeof(float), cudaMemcpyHostToDevice));
+        CREATE_CK(cudaMemcpy(A.inv_m, im.data(), na * sizeof(float), cudaMemcpyHostToDevice));
+        A.bstart = d_start;
+        A.bpart = d_part;
+        A.bk = d_bk;
+        A.br0 = d_br0;
+        C.X = A.X;
+        C.U = A.U;
+        C.J = A.J;
+    }
+    h->fix_grid = na > 0 ? (C.touched_cap + 255) / 256 : 1;
+    CREATE_CK(cudaStreamSynchronize(h->stream));
+    *out = h;
+#undef CREATE_TRY
+#undef CREATE_CK
+    return LBMD_OK;
+}
+
+void lbmd_destroy(lbmd_t h) {
+    if (!h) return;
+    if (h->stream || h->s_main) cudaStreamSynchronize(h->stream);
+    destroy_graph(h);
+    for (void *p : h->allocs) cudaFree(p);
+    if (h->stage) cudaFree(h->stage);
+    if (h->ev_fork) cudaEventDestroy(h->ev_fork);
+    if (h->ev_join) cudaEventDestroy(h->ev_join);
+    if (h->ev_t0) cudaEventDestroy(h->ev_t0);
+    if (h->ev_t1) cudaEventDestroy(h->ev_t1);
+    if (h->s_main) cudaStreamDestroy(h->s_main);
+    if (h->s_lat) cudaStreamDestroy(h->s_lat);
+    delete h;
+}
+
+lbmd_status lbmd_set_state(lbmd_t h, const float *f, const float *rho, const float *u, const double *x,
+                           const float *v, int on_device) {
+    if (!h) return fail(nullptr, LBMD_ERR_ARG, "handle is NULL");
+    if (!f && (!rho || !u)) return fail(h, LBMD_ERR_ARG, "give f, or rho and u");
+    if (h->na > 0 && (!x || !v)) return fail(h, LBMD_ERR_ARG, "x and v are required when n_atoms > 0");
+    const Lat &L = h->L;
+    const float *df = f, *drho = rho, *du = u;
+    if (!on_device) {
+        void *p;
+        CK(h, stage(h, L.N * (f ? Q : 4) * sizeof(float), &p));
+        if (f) {
+            TRY(to_device(h, p, f, L.N * Q * sizeof(float), 0));
+            df = (const float *)p;
+        } else {
+            TRY(to_device(h, p, rho, L.N * sizeof(float), 0));
+            TRY(to_device(h, (float *)p + L.N, u, 3 * L.N * sizeof(float), 0));
+            drho = (const float *)p;
+            du = (const float *)p + L.N;
+        }
+    }
+    CK(h, launch_lb_init(h->p.store, L, h->pop[0], f ? df : nullptr, f ? nullptr : drho, f ? nullptr : du, h->stream));
+    CK(h, cudaMemsetAsync(h->ds, 0, sizeof(DevState), h->stream));
+    CK(h, cudaMemsetAsync(h->C.tag, 0, L.N * sizeof(int), h->stream));
+    CK(h, cudaMemsetAsync(h->C.G, 0, L.N * sizeof(float4), h->stream));
+    if (h->na > 0) {
+        const size_t na3 = (size_t)3 * h->na;
+        TRY(to_device(h, h->A.X, x, na3 * sizeof(double), on_device));
+        TRY(to_device(h, h->A.V, v, na3 * sizeof(float), on_device));
+        const size_t B = (size_t)h->A.fold[0] * h->A.fold[1] * h->A.fold[2];
+        for (int g = 0; g < 3; ++g) {
+            CK(h, cudaMemsetAsync(h->A.count[g], 0, B * sizeof(int), h->stream));
+            CK(h, cudaMemsetAsync(h->A.bucket[g], 0, h->na * sizeof(int), h->stream));
+        }
+        CK(h, cudaMemsetAsync(h->A.J, 0, na3 * sizeof(float), h->stream));
+        CK(h, cudaMemsetAsync(h->A.U, 0, na3 * sizeof(float), h->stream));
+        CK(h, launch_md_prime(h->A, h->stream));
+    }
+    if (!on_device) CK(h, cudaStreamSynchronize(h->stream));  // the caller may reuse its buffers
+    h->state_set = true;
+    h->steps = 0;
+    return read_flags(h);
+}
+
+lbmd_status lbmd_step(lbmd_t h, int n_steps) {
+    if (!h) return fail(nullptr, LBMD_ERR_ARG, "handle is NULL");
+    if (n_steps < 0) return fail(h, LBMD_ERR_ARG, "n_steps must be >= 0");
+    if (!h->state_set) return fail(h, LBMD_ERR_STATE, "lbmd_set_state has not been called");
+    if (!h->exec) TRY(build_graph(h));
+    for (int i = 0; i < n_steps; ++i) {
+        CK(h, cudaGraphLaunch(h->exec, h->stream));
+        ++h->steps;
+        if (h->p.check_every > 0 && h->steps % h->p.check_every == 0) TRY(read_flags(h));
+    }
+    return LBMD_OK;
+}
+
+lbmd_status lbmd_get_fields(lbmd_t h, float *f, float *rho, float *u, double *x, float *v, int on_device) {
+    if (!h) return fail(nullptr, LBMD_ERR_ARG, "handle is NULL");
+    if (!h->state_set) return fail(h, LBMD_ERR_STATE, "lbmd_set_state has not been called");
+    const Lat &L = h->L;
+    const void *cur = h->pop[h->steps & 1];
+    if (f || rho || u) {
+        float *df = f, *drho = rho, *du = u;
+        if (!on_device) {
+            void *p;
+            CK(h, stage(h, L.N * (Q + 4) * sizeof(float), &p));
+            float *base = (float *)p;
+            df = f ? base : nullptr;
+            drho = rho ? base + L.N * Q : nullptr;
+            du = u ? base + L.N * (Q + 1) : nullptr;
+        }
+        CK(h, launch_lb_fields(h->p.store, L, cur, df, drho, du, h->ds, h->stream));
+        if (!on_device) {
+            if (f) CK(h, cudaMemcpyAsync(f, df, L.N * Q * sizeof(float), cudaMemcpyDeviceToHost, h->stream));
+            if (rho) CK(h, cudaMemcpyAsync(rho, drho, L.N * sizeof(float), cudaMemcpyDeviceToHost, h->stream));
+            if (u) CK(h, cudaMemcpyAsync(u, du, 3 * L.N * sizeof(float), cudaMemcpyDeviceToHost, h->stream));
+        }
+    }
+    const cudaMemcpyKind k = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    if (h->na > 0) {
+        if (x) CK(h, cudaMemcpyAsync(x, h->A.X, 3 * (size_t)h->na * sizeof(double), k, h->stream));
+        if (v) CK(h, cudaMemcpyAsync(v, h->A.V, 3 * (size_t)h->na * sizeof(float), k, h->stream));
+    }
+    if (!on_device) CK(h, cudaStreamSynchronize(h->stream));
+    return LBMD_OK;
+}
+
+lbmd_status lbmd_get_stats(lbmd_t h, double *mass, double mom_fluid[3], double mom_atoms[3]) {
+    if (!h) return fail(nullptr, LBMD_ERR_ARG, "handle is NULL");
+    if (!h->state_set) return fail(h, LBMD_ERR_STATE, "lbmd_set_state has not been called");
+    const Lat &L = h->L;
+    const void *cur = h->pop[h->steps & 1];
+    CK(h, launch_lb_reduce(h->p.store, L, cur, h->red, h->red_blocks, h->ds, h->stream));
+    CK(h, launch_reduce_finish(h->red, h->red_blocks, 4, h->red_out, h->stream));
+    double out[7] = {0, 0, 0, 0, 0, 0, 0};
+    if (h->na > 0) {
+        const int nb = std::min(h->red_blocks, (h->na + 255) / 256);
+        // Atom partials reuse the tail of the partial buffer after the lattice sum.
+        CK(h, launch_atom_momentum(h->A.V, h->A.mass, h->na, h->red, nb, h->ds, h->stream));
+        CK(h, launch_reduce_finish(h->red, nb, 3, h->red_out + 4, h->stream));
+        CK(h, cudaMemcpyAsync(out, h->red_out, 7 * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    } else {
+        CK(h, cudaMemcpyAsync(out, h->red_out, 4 * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    }
+    CK(h, cudaStreamSynchronize(h->stream));
+    if (mass) *mass = (double)L.N * h->p.rho0 + out[0];
+    if (mom_fluid)
+        for (int d = 0; d < 3; ++d) mom_fluid[d] = out[1 + d];
+    if (mom_atoms)
+        for (int d = 0; d < 3; ++d) mom_atoms[d] = out[4 + d];
+    return read_flags(h);
+}
+
+lbmd_status lbmd_check(lbmd_t h) {
+    if (!h) return fail(nullptr, LBMD_ERR_ARG, "handle is NULL");
+    return read_flags(h);
+}
+
+lbmd_status lbmd_cell_list(lbmd_t h, int32_t *cell_of, int32_t *neighbours, int32_t *nc, int on_device) {
+    if (!h) return fail(nullptr, LBMD_ERR_ARG, "handle is NULL");
+    if (!h->state_set) return fail(h, LBMD_ERR_STATE, "lbmd_set_state has not been called");
+    if (nc)
+        for (int d = 0; d < 3; ++d) nc[d] = h->A.nc[d];
+    if (h->na == 0 || (!cell_of && !neighbours)) return LBMD_OK;
+    int *dc = cell_of, *dn = neighbours;
+    if (!on_device) {
+        void *p;
+        CK(h, stage(h, 2 * (size_t)h->na * sizeof(int), &p));
+        dc = cell_of ? (int *)p : nullptr;
+        dn = neighbours ? (int *)p + h->na : nullptr;
+    }
+    CK(h, launch_md_diag(h->A, dc, dn, h->stream));
+    if (!on_device) {
+        if (cell_of) CK(h, cudaMemcpyAsync(cell_of, dc, h->na * sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+        if (neighbours)
+            CK(h, cudaMemcpyAsync(neighbours, dn, h->na * sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    }
+    CK(h, cudaStreamSynchronize(h->stream));
+    return LBMD_OK;
+}
+
+lbmd_status lbmd_set_physics(lbmd_t h, double gamma, double tau, double force_amp) {
+    if (!h) return fail(nullptr, LBMD_ERR_ARG, "handle is NULL");
+    if (!(tau > 0.5) || !(gamma >= 0) || !std::isfinite(force_amp) || !std::isfinite(gamma))
+        return fail(h, LBMD_ERR_ARG, "need tau > 1/2, gamma >= 0 and a finite force_amp");
+    h->p.gamma = gamma;
+    h->p.tau = tau;
+    h->p.force_amp = force_amp;
+    fill_physics(h);
+    destroy_graph(h);
+    return LBMD_OK;
+}
+
+lbmd_status lbmd_set_timing_events(lbmd_t h, void *ev_start, void *ev_stop) {
+    if (!h) return fail(nullptr, LBMD_ERR_ARG, "handle is NULL");
+    if ((ev_start == nullptr) != (ev_stop == nullptr)) return fail(h, LBMD_ERR_ARG, "give both events or neither");
+    if (!h->state_set) return fail(h, LBMD_ERR_STATE, "lbmd_set_state has not been called");
+    if (!h->exec) TRY(build_graph(h));
+    if (!h->node_t0 || !h->node_t1) return fail(h, LBMD_ERR_CUDA, "timing nodes missing from the step graph");
+    cudaEvent_t a = ev_start ? (cudaEvent_t)ev_start : h->ev_t0;
+    cudaEvent_t b = ev_stop ? (cudaEvent_t)ev_stop : h->ev_t1;
+    CK(h, cudaGraphExecEventRecordNodeSetEvent(h->exec, h->node_t0, a));
+    CK(h, cudaGraphExecEventRecordNodeSetEvent(h->exec, h->node_t1, b));
+    return LBMD_OK;
+}
+
+lbmd_status lbmd_backward(lbmd_t h, int n_steps, int ckpt_every, int observable, double *d_gamma, double *d_tau,
+                          double *d_force_amp, double *obs) {
+    (void)n_steps;
+    (void)ckpt_every;
+    (void)observable;
+    (void)d_gamma;
+    (void)d_tau;
+    (void)d_force_amp;
+    (void)obs;
+    if (!h) return fail(nullptr, LBMD_ERR_ARG, "handle is NULL");
+    return fail(h, LBMD_ERR_ARG, "lbmd_backward is not available in this build");
+}
+
+}  // extern "C"

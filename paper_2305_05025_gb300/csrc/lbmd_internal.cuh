@@ -1,0 +1,242 @@
+// Internal declarations of the sm_103a coupled LB-MD step: D3Q19 constants,
+// storage formats, kernel argument blocks and launcher prototypes. Shared by
+// the library's own translation units only.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/lbmd.h"
+
+namespace lbmd {
+
+constexpr int Q = 19;
+
+// D3Q19 speeds in the ABI order (rest, six faces, twelve edges; 2k-1 and 2k
+// opposite). Written as constant expressions so unrolled loops fold them.
+__host__ __device__ __forceinline__ constexpr int cx(int i) {
+    return (i == 1 || i == 7 || i == 9 || i == 11 || i == 13)     ? 1
+           : (i == 2 || i == 8 || i == 10 || i == 12 || i == 14) ? -1
+                                                                   : 0;
+}
+__host__ __device__ __forceinline__ constexpr int cy(int i) {
+    return (i == 3 || i == 7 || i == 10 || i == 15 || i == 17)    ? 1
+           : (i == 4 || i == 8 || i == 9 || i == 16 || i == 18)  ? -1
+                                                                   : 0;
+}
+__host__ __device__ __forceinline__ constexpr int cz(int i) {
+    return (i == 5 || i == 11 || i == 14 || i == 15 || i == 18)   ? 1
+           : (i == 6 || i == 12 || i == 13 || i == 16 || i == 17) ? -1
+                                                                    : 0;
+}
+__host__ __device__ __forceinline__ constexpr int opp(int i) { return i == 0 ? 0 : ((i & 1) ? i + 1 : i - 1); }
+__host__ __device__ __forceinline__ constexpr float wgt(int i) {
+    return i == 0 ? 1.0f / 3.0f : (i <= 6 ? 1.0f / 18.0f : 1.0f / 36.0f);
+}
+
+// Device error flags (bit mask), raised with atomicOr, read by the host.
+enum : int { FLAG_NONFINITE = 1, FLAG_CELL = 2, FLAG_WALL = 4, FLAG_TOUCHED = 8 };
+
+// Device-resident step state, updated by the last kernel of each step.
+struct DevState {
+    int step;        // coupled steps done since the last set_state
+    int n_touched;   // unique nodes claimed by atoms this step
+    int flags;       // FLAG_* bits
+    unsigned ticket; // last-block detection of the fix-up kernel
+};
+
+// Storage formats of the populations (delta f = f - w rho0 in every format).
+template <int S> struct Store;
+template <> struct Store<LBMD_F32> {
+    using T = float;
+    static __device__ __forceinline__ float ld(const T *p) { return __ldg(p); }
+    static __device__ __forceinline__ float ld_plain(const T *p) { return *p; }
+    static __device__ __forceinline__ void st(T *p, float v) { __stcs(p, v); }
+    static __device__ __forceinline__ void st_plain(T *p, float v) { *p = v; }
+};
+template <> struct Store<LBMD_F16_SHIFTED> {
+    using T = __half;
+    static __device__ __forceinline__ float ld(const T *p) { return __half2float(__ldg(p)); }
+    static __device__ __forceinline__ float ld_plain(const T *p) { return __half2float(*p); }
+    static __device__ __forceinline__ void st(T *p, float v) { __stcs(p, __float2half_rn(v)); }
+    static __device__ __forceinline__ void st_plain(T *p, float v) { *p = __float2half_rn(v); }
+};
+template <> struct Store<LBMD_BF16_SHIFTED> {
+    using T = __nv_bfloat16;
+    static __device__ __forceinline__ float ld(const T *p) { return __bfloat162float(__ldg(p)); }
+    static __device__ __forceinline__ float ld_plain(const T *p) { return __bfloat162float(*p); }
+    static __device__ __forceinline__ void st(T *p, float v) { __stcs(p, __float2bfloat16_rn(v)); }
+    static __device__ __forceinline__ void st_plain(T *p, float v) { *p = __float2bfloat16_rn(v); }
+};
+
+inline size_t store_bytes(int store) { return store == LBMD_F32 ? 4 : 2; }
+
+// Lattice description passed by value to every lattice kernel.
+struct Lat {
+    int nx, ny, nz;
+    size_t N;     // nx*ny*nz, also the plane stride of the SoA populations
+    float omega;  // 1/tau
+    float rho0;
+    int walls;    // z bounce-back walls
+    int forcing;  // LBMD_FORCE_*
+    float famp;   // body-force amplitude
+    int fdir, faxis;
+    float kwave;  // 2 / n_axis (sinpi argument scale of the Kolmogorov wave)
+};
+
+// Body force g at a node (analytic: costs no memory traffic).
+__device__ __forceinline__ void body_force(const Lat &L, int x, int y, int z, float g[3]) {
+    g[0] = g[1] = g[2] = 0.f;
+    if (L.forcing == LBMD_FORCE_NONE) return;
+    float a = L.famp;
+    if (L.forcing == LBMD_FORCE_KOLMOGOROV) {
+        int c = L.faxis == 0 ? x : (L.faxis == 1 ? y : z);
+        a *= sinpif(L.kwave * (float)c);
+    }
+    g[L.fdir] = a;
+}
+
+// Index of population i pulled into node (x, y, z): the post-collision value
+// h_i(x - c_i), or h_opp(i)(x) when x - c_i is behind a z wall (half-way
+// bounce-back). Periodic elsewhere.
+__device__ __forceinline__ size_t pull_index(const Lat &L, int i, int x, int y, int z, int xm, int xp, int ym,
+                                             int yp, int zm, int zp, size_t node) {
+    const int sx = cx(i) == 1 ? xm : (cx(i) == -1 ? xp : x);
+    const int sy = cy(i) == 1 ? ym : (cy(i) == -1 ? yp : y);
+    const int sz = cz(i) == 1 ? zm : (cz(i) == -1 ? zp : z);
+    bool wall = false;
+    if (L.walls) wall = (cz(i) == 1 && z == 0) || (cz(i) == -1 && z == L.nz - 1);
+    return wall ? (size_t)opp(i) * L.N + node : (size_t)i * L.N + ((size_t)sz * L.ny + sy) * L.nx + sx;
+}
+
+template <int S>
+__device__ __forceinline__ void pull(const typename Store<S>::T *__restrict__ src, const Lat &L, int x, int y,
+                                     int z, float f[Q]) {
+    const int xm = x == 0 ? L.nx - 1 : x - 1, xp = x == L.nx - 1 ? 0 : x + 1;
+    const int ym = y == 0 ? L.ny - 1 : y - 1, yp = y == L.ny - 1 ? 0 : y + 1;
+    const int zm = z == 0 ? L.nz - 1 : z - 1, zp = z == L.nz - 1 ? 0 : z + 1;
+    const size_t node = ((size_t)z * L.ny + y) * L.nx + x;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) f[i] = Store<S>::ld(src + pull_index(L, i, x, y, z, xm, xp, ym, yp, zm, zp, node));
+}
+
+// BGK collision with the Guo source on deviations (Eq. 1, standard minus
+// sign): f_i <- f_i - omega (f_i - f_eq_i) + (1 - omega/2) w_i [3(c_i - u) +
+// 9 (c_i.u) c_i].F with u = (sum f c + F/2)/rho; every value shifted by
+// w_i rho0. Returns rho.
+__device__ __forceinline__ float collide(const Lat &L, float f[Q], const float F[3]) {
+    float drho = 0.f, jx = 0.f, jy = 0.f, jz = 0.f;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        drho += f[i];
+        if (cx(i)) jx += cx(i) * f[i];
+        if (cy(i)) jy += cy(i) * f[i];
+        if (cz(i)) jz += cz(i) * f[i];
+    }
+    const float rho = L.rho0 + drho;
+    const float inv = 1.f / rho;
+    const float ux = (jx + 0.5f * F[0]) * inv, uy = (jy + 0.5f * F[1]) * inv, uz = (jz + 0.5f * F[2]) * inv;
+    const float usq = ux * ux + uy * uy + uz * uz;
+    const float uF = ux * F[0] + uy * F[1] + uz * F[2];
+    const float om = L.omega, src = 1.f - 0.5f * om;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        const float cu = cx(i) * ux + cy(i) * uy + cz(i) * uz;
+        const float cF = cx(i) * F[0] + cy(i) * F[1] + cz(i) * F[2];
+        const float feq = wgt(i) * (drho + rho * (3.f * cu + 4.5f * cu * cu - 1.5f * usq));
+        const float S = src * wgt(i) * (3.f * (cF - uF) + 9.f * cu * cF);
+        f[i] = f[i] - om * (f[i] - feq) + S;
+    }
+    return rho;
+}
+
+// Velocity u = (sum f c + g/2)/rho of a node from its pulled deviations.
+__device__ __forceinline__ float node_velocity(const Lat &L, const float f[Q], const float g[3], float u[3]) {
+    float drho = 0.f, jx = 0.f, jy = 0.f, jz = 0.f;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        drho += f[i];
+        if (cx(i)) jx += cx(i) * f[i];
+        if (cy(i)) jy += cy(i) * f[i];
+        if (cz(i)) jz += cz(i) * f[i];
+    }
+    const float rho = L.rho0 + drho;
+    const float inv = 1.f / rho;
+    u[0] = (jx + 0.5f * g[0]) * inv;
+    u[1] = (jy + 0.5f * g[1]) * inv;
+    u[2] = (jz + 0.5f * g[2]) * inv;
+    return rho;
+}
+
+// ---------------------------------------------------------------------------
+// Atoms.
+//
+// Positions: X (FP64, unwrapped) is the accumulator, advanced once per coupled
+// step. Inside a step each atom carries FP32 coordinates P relative to the
+// corner of a reference cell cref (fixed for the step), advanced with
+// compensated (two-sum) FP32 sums, so pair displacements are small FP32
+// differences: d = wrap(cref_a - cref_b) h + (P_a - P_b).
+
+constexpr int CREF_BITS = 10;  // cref packs three cell coordinates < 1024
+
+struct AtomArgs {
+    int na;
+    int n_md;
+    float dt, hdt;        // 1/n_md and half of it
+    float gamma;
+    float lj_sig2, lj_24eps, lj_fc, rc2f;  // LJ constants; lj_fc = F_LJ(rc)
+    double rc2d;          // rc^2 in FP64 (neighbour counts)
+    int nc[3];            // cell grid (side h = L/nc >= rc + skin)
+    int fold[3];          // bucket grid: cell c -> bucket c mod fold
+    int cap;              // slots per bucket
+    float h[3], inv_h[3];
+    double hd[3], Ld[3];
+    double *X;            // 3*na FP64 accumulator
+    float4 *P[2];         // (Px, Py, Pz, cref bits) by substep parity
+    float *P0, *Plo;      // 3*na step-start offsets and two-sum compensation
+    float *V, *F, *U, *J; // 3*na SoA each
+    float *mass, *inv_m;
+    const int *bstart, *bpart;  // bond CSR
+    const float *bk, *br0;
+    int *count[3], *slot[3], *bucket[3];  // pair-search buckets by generation mod 3
+    DevState *ds;
+};
+
+struct CouplingArgs {
+    Lat L;
+    int na;
+    const double *X;
+    float *U, *J;
+    int *base;      // 3*na wrapped base node per atom (step start)
+    float *frac;    // 3*na fractional offsets (step start)
+    int *tag;       // per node: step stamp of the last claim
+    int *touched;   // unique touched nodes of this step
+    int touched_cap;
+    float4 *G;      // per node coupling force (x, y, z, unused)
+    DevState *ds;
+};
+
+// Launchers (stream-ordered, no synchronisation).
+cudaError_t launch_lb_step(int store, const Lat &L, void *const buf[2], DevState *ds, cudaStream_t s);
+cudaError_t launch_lb_fix(int store, const Lat &L, void *const buf[2], const CouplingArgs &c, int grid,
+                          cudaStream_t s);
+cudaError_t launch_lb_fields(int store, const Lat &L, const void *cur, float *f, float *rho, float *u,
+                             DevState *ds, cudaStream_t s);
+cudaError_t launch_lb_init(int store, const Lat &L, void *dst, const float *f, const float *rho, const float *u,
+                           cudaStream_t s);
+cudaError_t launch_lb_reduce(int store, const Lat &L, const void *cur, double *partials, int nblocks, DevState *ds,
+                             cudaStream_t s);
+cudaError_t launch_reduce_finish(const double *partials, int nblocks, int width, double *out, cudaStream_t s);
+cudaError_t launch_atom_momentum(const float *V, const float *mass, int na, double *partials, int nblocks,
+                                 DevState *ds, cudaStream_t s);
+
+cudaError_t launch_md_prime(const AtomArgs &a, cudaStream_t s);
+cudaError_t launch_md_substep(const AtomArgs &a, int k, cudaStream_t s);
+cudaError_t launch_md_diag(const AtomArgs &a, int *cell_of, int *neigh, cudaStream_t s);
+
+cudaError_t launch_interp(int store, const CouplingArgs &c, const AtomArgs &a, void *const buf[2], cudaStream_t s);
+cudaError_t launch_spread(const CouplingArgs &c, cudaStream_t s);
+
+}  // namespace lbmd

@@ -1,0 +1,105 @@
+"""GPU parity of the lattice part (fused pull-stream + BGK + Guo, Eq. 1) against
+the FP64 oracle, through the C ABI: rest fixed point, free-running multi-step
+parity on ragged lattice sizes (periodic with Kolmogorov forcing; z walls with
+Poiseuille forcing), state round trip, and the FP16/BF16 shifted storage."""
+import numpy as np
+import pytest
+
+from paper_2305_05025_gb300 import build, lbmd, synth
+from gpu_helpers import lattice_inputs, make, oracle_start, rel_linf, velocity
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-5  # relative L-infinity, FP32 against FP64
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    build.build()
+    lbmd.lib()
+
+
+def _cfg(**kw):
+    base = dict(synth._COMMON, nx=20, ny=18, nz=16, tau=0.6)
+    base.update(kw)
+    return base
+
+
+@pytest.mark.parametrize("store", ["f32", "f16", "bf16"])
+@pytest.mark.parametrize("walls", [0, 1])
+def test_rest_state_is_bit_exact(store, walls):
+    cfg = _cfg(store=store, walls_z=walls, nx=17, ny=9, nz=6)
+    inp = lattice_inputs((17, 9, 6), 0.0, 1)
+    h = make(cfg, inp)
+    lbmd.lbmd_step(h, 25)
+    out = lbmd.lbmd_get_fields(h, f=True, rho=True, u=True)
+    w = np.array([1 / 3] + [1 / 18] * 6 + [1 / 36] * 12, np.float32)
+    assert np.array_equal(out["f"], np.repeat(w[:, None], 17 * 9 * 6, axis=1))
+    assert np.all(out["rho"] == np.float32(1.0))
+    assert np.all(out["u"] == 0.0)
+    mass, pf, _ = lbmd.lbmd_get_stats(h)
+    assert mass == 17 * 9 * 6 and np.all(pf == 0.0)
+
+
+def _free_run(orc, cfg, inp, steps):
+    h = make(cfg, inp)
+    f, _, _, topo = oracle_start(orc, cfg, inp)
+    lbmd.lbmd_step(h, steps)
+    g = lbmd.lbmd_get_fields(h, f=True, rho=True, u=True)
+    fo, _, _, _ = orc.run(cfg, topo, f, np.zeros((3, 0)), np.zeros((3, 0)), steps)
+    return g, fo
+
+
+@pytest.mark.parametrize("tau", [0.55, 0.8])
+def test_periodic_kolmogorov_matches_oracle(orc, tau):
+    cfg = _cfg(tau=tau, forcing="kolmogorov", force_amp=1e-4, force_dir=0, force_wave_axis=1)
+    inp = lattice_inputs((20, 18, 16), 0.01, 3)
+    g, fo = _free_run(orc, cfg, inp, 100)
+    assert rel_linf(g["f"], fo) < TOL
+    uo = velocity(orc, cfg, fo)
+    assert rel_linf(g["u"], uo) < TOL
+    assert rel_linf(g["rho"] - 1.0, orc.moments(fo)[0] - 1.0) < 1e-3  # density deviations ~1e-4
+
+
+def test_walls_poiseuille_matches_oracle(orc):
+    cfg = _cfg(nx=8, ny=6, nz=20, tau=0.8, walls_z=1, forcing="poiseuille", force_amp=1e-5)
+    inp = lattice_inputs((8, 6, 20), 0.005, 4)
+    g, fo = _free_run(orc, cfg, inp, 100)
+    assert rel_linf(g["f"], fo) < TOL
+    assert rel_linf(g["u"], velocity(orc, cfg, fo)) < TOL
+
+
+def test_uniform_forcing_along_z_matches_oracle(orc):
+    cfg = _cfg(nx=33, ny=5, nz=7, tau=1.3, forcing="uniform", force_amp=3e-5, force_dir=2)
+    inp = lattice_inputs((33, 5, 7), 0.02, 5)
+    g, fo = _free_run(orc, cfg, inp, 60)
+    assert rel_linf(g["f"], fo) < TOL
+    assert rel_linf(g["u"], velocity(orc, cfg, fo)) < TOL
+
+
+def test_state_round_trip():
+    cfg = _cfg(nx=13, ny=7, nz=5, walls_z=1)
+    N = 13 * 7 * 5
+    rng = np.random.default_rng(6)
+    w = np.array([1 / 3] + [1 / 18] * 6 + [1 / 36] * 12)
+    f = (w[:, None] * (1 + 0.05 * rng.standard_normal((19, N)))).astype(np.float32)
+    h = lbmd.lbmd_create(cfg)
+    lbmd.lbmd_set_state(h, f=f)
+    back = lbmd.lbmd_get_fields(h, f=True)["f"]
+    # delta f = f - w rho0 and back: at most one FP32 rounding each way.
+    assert np.abs(back - f).max() <= 2 * np.finfo(np.float32).eps * 0.4
+
+
+@pytest.mark.parametrize("store,bound", [("f16", 2e-3), ("bf16", 2e-2)])
+def test_shifted_storage_error_is_bounded(orc, store, bound):
+    """FP16/BF16 store delta f = f - w rho0 with FP32 arithmetic: the error
+    against the FP64 oracle stays at the storage format's resolution of delta f
+    (FP16: 2^-11, BF16: 2^-8 relative), reported per field."""
+    cfg = _cfg(tau=0.6, store=store, forcing="kolmogorov", force_amp=1e-4)
+    inp = lattice_inputs((20, 18, 16), 0.01, 7)
+    g, fo = _free_run(orc, cfg, inp, 100)
+    w = np.array([1 / 3] + [1 / 18] * 6 + [1 / 36] * 12)
+    df_err = rel_linf(g["f"] - w[:, None], fo - w[:, None])
+    u_err = rel_linf(g["u"], velocity(orc, cfg, fo))
+    print(f"{store}: delta f rel Linf {df_err:.3e}, u rel Linf {u_err:.3e}")
+    assert df_err < bound and u_err < bound
