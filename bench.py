@@ -31,7 +31,7 @@ sys.path.insert(0, ROOT)
 from paper_2305_05025_gb300 import synth  # noqa: E402
 
 DEFAULT_WORKLOAD = "globule20k_lattice128"
-# Workload choices not fixed by the workload description:
+# Choices the workload description leaves open:
 # n_md resolves the LJ repulsion, gamma keeps the explicit friction exchange
 # stable once the globule is dense.
 DEFAULT_OVERRIDES = dict(n_md=128, gamma=0.05)
@@ -213,6 +213,10 @@ def run_ours(args, cfg):
     with Clocks(local) as clk:
         t0.record(stream)
         for i in range(args.steps):
+            # torch only reads events it recorded itself: record both here; the
+            # graph's record nodes (later on the same stream) set the times used.
+            ev[i][0].record(stream)
+            ev[i][1].record(stream)
             lbmd.lbmd_set_timing_events(h, ev[i][0], ev[i][1])
             lbmd.lbmd_step(h, 1)
         t1.record(stream)

@@ -31,7 +31,7 @@ __global__ void __launch_bounds__(128) k_interp(CouplingArgs C, AtomArgs A, cons
     double x[3];
     bool finite = true;
     int cr[3];
-    float p0[3];
+    float p0[3], r0[3];
     for (int d = 0; d < 3; ++d) {
         x[d] = C.X[d * na + a];
         finite = finite && isfinite(x[d]);
@@ -39,13 +39,16 @@ __global__ void __launch_bounds__(128) k_interp(CouplingArgs C, AtomArgs A, cons
         double fl = floor(s);
         if (!(fabs(fl) < 4.0e15)) fl = 0.0;
         cr[d] = wrapl((long long)fl, A.nc[d]);
-        p0[d] = (float)((s - fl) * A.hd[d]);
+        const double off = (s - fl) * A.hd[d];
+        p0[d] = (float)off;
+        r0[d] = (float)(off - (double)p0[d]);
         A.P0[d * na + a] = p0[d];
-        A.Plo[d * na + a] = 0.f;
+        A.R0[d * na + a] = r0[d];
     }
     A.P[par][a] = make_float4(p0[0], p0[1], p0[2],
                               __uint_as_float((unsigned)cr[0] | ((unsigned)cr[1] << CREF_BITS) |
                                               ((unsigned)cr[2] << (2 * CREF_BITS))));
+    A.L[par][a] = make_float4(r0[0], r0[1], r0[2], 0.f);
     if (!finite) atomicOr(&C.ds->flags, FLAG_NONFINITE);
 
     int b[3];

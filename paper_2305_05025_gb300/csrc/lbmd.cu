@@ -195,6 +195,7 @@ void fill_physics(lbmd_t h) {
         A.hd[d] = (double)Ls[d] / A.nc[d];
         A.h[d] = (float)A.hd[d];
         A.inv_h[d] = (float)(A.nc[d] / (double)Ls[d]);
+        A.h_lo[d] = (float)(A.hd[d] - (double)A.h[d]);
     }
     A.cap = kCap;
     h->C.L = L;
@@ -368,8 +369,10 @@ lbmd_status lbmd_create(const lbmd_params *params, int n_atoms, const double *ma
         CREATE_TRY(dalloc_t(h, &A.X, na3));
         CREATE_TRY(dalloc_t(h, &A.P[0], (size_t)na));
         CREATE_TRY(dalloc_t(h, &A.P[1], (size_t)na));
+        CREATE_TRY(dalloc_t(h, &A.L[0], (size_t)na));
+        CREATE_TRY(dalloc_t(h, &A.L[1], (size_t)na));
         CREATE_TRY(dalloc_t(h, &A.P0, na3));
-        CREATE_TRY(dalloc_t(h, &A.Plo, na3));
+        CREATE_TRY(dalloc_t(h, &A.R0, na3));
         CREATE_TRY(dalloc_t(h, &A.V, na3));
         CREATE_TRY(dalloc_t(h, &A.F, na3));
         CREATE_TRY(dalloc_t(h, &A.U, na3));
@@ -487,6 +490,8 @@ lbmd_status lbmd_set_state(lbmd_t h, const float *f, const float *rho, const flo
         CK(h, cudaMemsetAsync(h->A.U, 0, na3 * sizeof(float), h->stream));
         CK(h, launch_md_prime(h->A, h->stream));
     }
+    // Scan the new lattice for NaN/Inf (raises the flag read below).
+    CK(h, launch_lb_reduce(h->p.store, L, h->pop[0], h->red, h->red_blocks, h->ds, h->stream));
     if (!on_device) CK(h, cudaStreamSynchronize(h->stream));  // the caller may reuse its buffers
     h->state_set = true;
     h->steps = 0;

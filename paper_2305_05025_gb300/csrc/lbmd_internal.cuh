@@ -174,10 +174,11 @@ __device__ __forceinline__ float node_velocity(const Lat &L, const float f[Q], c
 // Atoms.
 //
 // Positions: X (FP64, unwrapped) is the accumulator, advanced once per coupled
-// step. Inside a step each atom carries FP32 coordinates P relative to the
-// corner of a reference cell cref (fixed for the step), advanced with
-// compensated (two-sum) FP32 sums, so pair displacements are small FP32
-// differences: d = wrap(cref_a - cref_b) h + (P_a - P_b).
+// step. Inside a step each atom carries its offset from the corner of a
+// reference cell cref (fixed for the step) as an unevaluated FP32 pair
+// hi + lo, advanced with error-free (two-sum) updates, so a pair displacement
+// d = wrap(cref_a - cref_b) h + (hi_a - hi_b) + (lo_a - lo_b) carries ~2^-44
+// relative error before its final rounding.
 
 constexpr int CREF_BITS = 10;  // cref packs three cell coordinates < 1024
 
@@ -194,8 +195,10 @@ struct AtomArgs {
     float h[3], inv_h[3];
     double hd[3], Ld[3];
     double *X;            // 3*na FP64 accumulator
-    float4 *P[2];         // (Px, Py, Pz, cref bits) by substep parity
-    float *P0, *Plo;      // 3*na step-start offsets and two-sum compensation
+    float4 *P[2];         // (hi x, hi y, hi z, cref bits) by substep parity
+    float4 *L[2];         // (lo x, lo y, lo z, 0) by substep parity
+    float *P0, *R0;       // 3*na step-start hi and lo parts
+    float h_lo[3];        // hd - (double)h
     float *V, *F, *U, *J; // 3*na SoA each
     float *mass, *inv_m;
     const int *bstart, *bpart;  // bond CSR

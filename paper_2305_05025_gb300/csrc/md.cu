@@ -45,6 +45,51 @@ __device__ __forceinline__ void disp(const AtomArgs &A, float4 pa, const int ca[
     d[2] = (float)wrapdiff(ca[2] - cb[2], A.nc[2]) * A.h[2] + (pa.z - pb.z);
 }
 
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
+    s = a + b;
+    const float bp = s - a;
+    e = (a - (s - bp)) + (b - bp);
+}
+
+// x_a - x_b as an unevaluated pair dh + dl (error-free transformations).
+__device__ __forceinline__ void disp_df(const AtomArgs &A, float4 pa, float4 la, const int ca[3], float4 pb,
+                                        float4 lb, float dh[3], float dl[3]) {
+    int cb[3];
+    unpack_cref(pb.w, cb);
+    const float ha[3] = {pa.x, pa.y, pa.z}, hb[3] = {pb.x, pb.y, pb.z};
+    const float la3[3] = {la.x, la.y, la.z}, lb3[3] = {lb.x, lb.y, lb.z};
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        const float dc = (float)wrapdiff(ca[d] - cb[d], A.nc[d]);
+        float s, e, s2, e2;
+        two_sum(ha[d], -hb[d], s, e);
+        two_sum(dc * A.h[d], s, s2, e2);
+        dh[d] = s2;
+        dl[d] = (e + e2) + ((la3[d] - lb3[d]) + dc * A.h_lo[d]);
+    }
+}
+
+// Harmonic bond force factor -k (r - r0) / r with r - r0 evaluated as
+// (r^2 - r0^2) / (r + r0) from a compensated r^2, so the stretch keeps its
+// relative precision when r is close to r0.
+__device__ __forceinline__ float bond_factor(const float dh[3], const float dl[3], float k, float r0) {
+    float p[3], pe[3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        p[d] = dh[d] * dh[d];
+        pe[d] = fmaf(dh[d], dh[d], -p[d]) + 2.f * dh[d] * dl[d];
+    }
+    float s01, e01, s, e;
+    two_sum(p[0], p[1], s01, e01);
+    two_sum(s01, p[2], s, e);
+    const float r2_lo = (e01 + e) + (pe[0] + pe[1] + pe[2]);
+    const float r0sq = r0 * r0;
+    const float r0sq_lo = fmaf(r0, r0, -r0sq);
+    const float diff = (s - r0sq) + (r2_lo - r0sq_lo);
+    const float r = sqrtf(s);
+    return -k * (diff / (r + r0)) / r;
+}
+
 __device__ __forceinline__ int bucket_of(const AtomArgs &A, const int c[3]) {
     return ((c[2] % A.fold[2]) * A.fold[1] + (c[1] % A.fold[1])) * A.fold[0] + (c[0] % A.fold[0]);
 }
@@ -62,46 +107,85 @@ __device__ __forceinline__ bool bonded(const AtomArgs &A, int a, int b) {
     return false;
 }
 
-// Conservative force on atom a at the positions P (buckets of generation g3).
-__device__ void md_force(const AtomArgs &A, const float4 *__restrict__ P, int g3, int a, float4 pa, float F[3]) {
+// Conservative force on atom a at the positions P (buckets of generation g3),
+// evaluated by a whole warp: the candidates of the 27 neighbour cells are
+// numbered through a warp prefix sum over the cell counts and dealt round-robin
+// to the lanes (so every lane has about the same number of dependent loads in
+// flight), bonds are dealt the same way, and the three force components are
+// summed across the warp. Every lane returns the full force.
+__device__ void md_force_warp(const AtomArgs &A, const float4 *__restrict__ P, const float4 *__restrict__ Lq, int g3,
+                              int a, float4 pa, float4 la, float F[3]) {
+    const int lane = threadIdx.x & 31;
     int ca[3], cc[3];
     unpack_cref(pa.w, ca);
     current_cell(A, pa, ca, cc);
-    float fx = 0.f, fy = 0.f, fz = 0.f;
     const int *__restrict__ cnt = A.count[g3];
     const int *__restrict__ slots = A.slot[g3];
-    for (int oz = -1; oz <= 1; ++oz)
-        for (int oy = -1; oy <= 1; ++oy)
-            for (int ox = -1; ox <= 1; ++ox) {
-                const int c[3] = {wrapi(cc[0] + ox, A.nc[0]), wrapi(cc[1] + oy, A.nc[1]), wrapi(cc[2] + oz, A.nc[2])};
-                const int b = bucket_of(A, c);
-                const int n = min(cnt[b], A.cap);
-                const int *s = slots + (size_t)b * A.cap;
-                for (int j = 0; j < n; ++j) {
-                    const int q = s[j];
-                    if (q == a) continue;
-                    float d[3];
-                    disp(A, pa, ca, P[q], d);
-                    const float r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
-                    if (!(r2 < A.rc2f)) continue;
-                    if (bonded(A, a, q)) continue;
-                    const float inv_r2 = 1.0f / r2;
-                    const float sr2 = A.lj_sig2 * inv_r2;
-                    const float sr6 = sr2 * sr2 * sr2;
-                    const float fr = A.lj_24eps * inv_r2 * sr6 * (2.f * sr6 - 1.f) - A.lj_fc * rsqrtf(r2);
-                    fx += fr * d[0];
-                    fy += fr * d[1];
-                    fz += fr * d[2];
-                }
-            }
-    for (int s = A.bstart[a]; s < A.bstart[a + 1]; ++s) {
+    // Lane k < 27 owns neighbour cell k: its bucket and candidate count.
+    int bucket = 0, n = 0;
+    if (lane < 27) {
+        const int ox = lane % 3 - 1, oy = (lane / 3) % 3 - 1, oz = lane / 9 - 1;
+        const int c[3] = {wrapi(cc[0] + ox, A.nc[0]), wrapi(cc[1] + oy, A.nc[1]), wrapi(cc[2] + oz, A.nc[2])};
+        bucket = bucket_of(A, c);
+        n = min(cnt[bucket], A.cap);
+    }
+    int incl = n;  // inclusive prefix sum over lanes
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += t;
+    }
+    const int total = __shfl_sync(0xffffffffu, incl, 31);
+    float fx = 0.f, fy = 0.f, fz = 0.f;
+    for (int t = lane; t - lane < total; t += 32) {
+        // Cell holding candidate t: first lane whose inclusive sum exceeds t.
+        int pos = 0;
+#pragma unroll
+        for (int step = 16; step > 0; step >>= 1) {
+            const int probe = __shfl_sync(0xffffffffu, incl, pos + step - 1);
+            if (probe <= t) pos += step;
+        }
+        const int cb = __shfl_sync(0xffffffffu, bucket, pos & 31);
+        const int before = __shfl_sync(0xffffffffu, incl - n, pos & 31);
+        if (t >= total) continue;
+        const int q = slots[(size_t)cb * A.cap + (t - before)];
+        if (q == a) continue;
+        const float4 pq = P[q];
         float d[3];
-        disp(A, pa, ca, P[A.bpart[s]], d);
-        const float r = sqrtf(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
-        const float fr = -A.bk[s] * (r - A.br0[s]) / r;
+        disp(A, pa, ca, pq, d);
+        if (!(d[0] * d[0] + d[1] * d[1] + d[2] * d[2] < A.rc2f * 1.0001f)) continue;
+        {
+            float dh[3], dl[3];
+            disp_df(A, pa, la, ca, pq, Lq[q], dh, dl);
+            d[0] = dh[0] + dl[0];
+            d[1] = dh[1] + dl[1];
+            d[2] = dh[2] + dl[2];
+        }
+        const float r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+        if (!(r2 < A.rc2f)) continue;
+        if (bonded(A, a, q)) continue;
+        const float inv_r2 = 1.0f / r2;
+        const float sr2 = A.lj_sig2 * inv_r2;
+        const float sr6 = sr2 * sr2 * sr2;
+        const float fr = A.lj_24eps * inv_r2 * sr6 * (2.f * sr6 - 1.f) - A.lj_fc * rsqrtf(r2);
         fx += fr * d[0];
         fy += fr * d[1];
         fz += fr * d[2];
+    }
+    for (int s = A.bstart[a] + lane; s < A.bstart[a + 1]; s += 32) {
+        const int q = A.bpart[s];
+        float dh[3], dl[3];
+        disp_df(A, pa, la, ca, P[q], Lq[q], dh, dl);
+        const float fr = bond_factor(dh, dl, A.bk[s], A.br0[s]);
+        fx += fr * (dh[0] + dl[0]);
+        fy += fr * (dh[1] + dl[1]);
+        fz += fr * (dh[2] + dl[2]);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        fx += __shfl_xor_sync(0xffffffffu, fx, o);
+        fy += __shfl_xor_sync(0xffffffffu, fy, o);
+        fz += __shfl_xor_sync(0xffffffffu, fz, o);
     }
     F[0] = fx;
     F[1] = fy;
@@ -132,7 +216,7 @@ __global__ void k_prime_insert(AtomArgs A) {
     const int a = blockIdx.x * blockDim.x + threadIdx.x;
     if (a >= A.na) return;
     int cr[3];
-    float p0[3];
+    float p0[3], r0[3];
     bool finite = true;
     for (int d = 0; d < 3; ++d) {
         const double x = A.X[d * A.na + a];
@@ -142,12 +226,15 @@ __global__ void k_prime_insert(AtomArgs A) {
         if (!(fabs(fl) < 4.0e15)) fl = 0.0;
         long long c = (long long)fl % A.nc[d];
         cr[d] = (int)(c < 0 ? c + A.nc[d] : c);
-        p0[d] = (float)((s - fl) * A.hd[d]);
+        const double off = (s - fl) * A.hd[d];
+        p0[d] = (float)off;
+        r0[d] = (float)(off - (double)p0[d]);
         A.P0[d * A.na + a] = p0[d];
-        A.Plo[d * A.na + a] = 0.f;
+        A.R0[d * A.na + a] = r0[d];
     }
     if (!finite) atomicOr(&A.ds->flags, FLAG_NONFINITE);
     A.P[0][a] = make_float4(p0[0], p0[1], p0[2], pack_cref(cr));
+    A.L[0][a] = make_float4(r0[0], r0[1], r0[2], 0.f);
     int c[3];
     for (int d = 0; d < 3; ++d) c[d] = exact_cell(A.X[d * A.na + a], A.nc[d], A.Ld[d]);
     insert(A, 0, a, c);
@@ -156,28 +243,35 @@ __global__ void k_prime_insert(AtomArgs A) {
 }
 
 __global__ void k_prime_force(AtomArgs A) {
-    const int a = blockIdx.x * blockDim.x + threadIdx.x;
+    const int a = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (a >= A.na) return;
     float F[3];
-    md_force(A, A.P[0], 0, a, A.P[0][a], F);
-    for (int d = 0; d < 3; ++d) A.F[d * A.na + a] = F[d];
+    md_force_warp(A, A.P[0], A.L[0], 0, a, A.P[0][a], A.L[0][a], F);
+    if ((threadIdx.x & 31) == 0)
+        for (int d = 0; d < 3; ++d) A.F[d * A.na + a] = F[d];
 }
 
+// One warp per atom: the warp evaluates the force, lane 0 integrates.
 __global__ void __launch_bounds__(128) k_md_substep(AtomArgs A, int k) {
-    const int a = blockIdx.x * blockDim.x + threadIdx.x;
+    // With programmatic dependent launch this kernel may start before the
+    // previous substep has finished: wait for its results first.
+    cudaGridDependencySynchronize();
+    const int a = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (a >= A.na) return;
     const long long gen = (long long)A.ds->step * A.n_md + k;
     const int par = (int)(gen & 1);
     const int g3 = (int)(gen % 3), gn3 = (int)((gen + 1) % 3), gp3 = (int)((gen + 2) % 3);
     const float4 pa = A.P[par][a];
+    const float4 la = A.L[par][a];
     const int na = A.na;
 
     float F[3];
     if (k == 0) {
         for (int d = 0; d < 3; ++d) F[d] = A.F[d * na + a];
     } else {
-        md_force(A, A.P[par], g3, a, pa, F);
+        md_force_warp(A, A.P[par], A.L[par], g3, a, pa, la, F);
     }
+    if ((threadIdx.x & 31) != 0) return;
     float v[3], U[3], J[3];
     const float im = A.inv_m[a];
     for (int d = 0; d < 3; ++d) {
@@ -198,19 +292,20 @@ __global__ void __launch_bounds__(128) k_md_substep(AtomArgs A, int k) {
             J[d] += A.hdt * drag;
             v[d] += A.hdt * (F[d] + drag) * im;
         }
-        float p[3] = {pa.x, pa.y, pa.z};
+        float p[3] = {pa.x, pa.y, pa.z}, lo[3] = {la.x, la.y, la.z};
         for (int d = 0; d < 3; ++d) {
-            // Compensated sum p + v dt (two-sum plus the exact product error).
+            // Error-free update of hi + lo by v dt (two-sum plus the exact
+            // product error).
             const float inc = v[d] * A.dt;
             const float e_mul = fmaf(v[d], A.dt, -inc);
-            const float s = p[d] + inc;
-            const float bp = s - p[d];
-            const float e_add = (p[d] - (s - bp)) + (inc - bp);
+            float s, e_add;
+            two_sum(p[d], inc, s, e_add);
             p[d] = s;
-            A.Plo[d * na + a] += e_add + e_mul;
+            lo[d] += e_add + e_mul;
         }
         const float4 pn = make_float4(p[0], p[1], p[2], pa.w);
         A.P[par ^ 1][a] = pn;
+        A.L[par ^ 1][a] = make_float4(lo[0], lo[1], lo[2], 0.f);
         A.count[gp3][A.bucket[gp3][a]] = 0;
         int cr[3], c[3];
         unpack_cref(pa.w, cr);
@@ -220,10 +315,11 @@ __global__ void __launch_bounds__(128) k_md_substep(AtomArgs A, int k) {
     } else {
         // End of the coupled step: cache the force and advance the FP64
         // accumulator by the compensated displacement.
-        const float pc[3] = {pa.x, pa.y, pa.z};
+        const float pc[3] = {pa.x, pa.y, pa.z}, lc[3] = {la.x, la.y, la.z};
         for (int d = 0; d < 3; ++d) {
             A.F[d * na + a] = F[d];
-            const double disp64 = ((double)pc[d] - (double)A.P0[d * na + a]) + (double)A.Plo[d * na + a];
+            const double disp64 = ((double)pc[d] - (double)A.P0[d * na + a]) +
+                                  ((double)lc[d] - (double)A.R0[d * na + a]);
             A.X[d * na + a] += disp64;
         }
     }
@@ -293,16 +389,23 @@ __global__ void k_md_diag(AtomArgs A, int *cell_of, int *neigh) {
 
 cudaError_t launch_md_prime(const AtomArgs &a, cudaStream_t s) {
     if (a.na == 0) return cudaSuccess;
-    const int grid = (a.na + 127) / 128;
-    k_prime_insert<<<grid, 128, 0, s>>>(a);
-    k_prime_force<<<grid, 128, 0, s>>>(a);
+    k_prime_insert<<<(a.na + 127) / 128, 128, 0, s>>>(a);
+    k_prime_force<<<(a.na + 3) / 4, 128, 0, s>>>(a);
     return cudaGetLastError();
 }
 
 cudaError_t launch_md_substep(const AtomArgs &a, int k, cudaStream_t s) {
     if (a.na == 0) return cudaSuccess;
-    k_md_substep<<<(a.na + 127) / 128, 128, 0, s>>>(a, k);
-    return cudaGetLastError();
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((a.na + 3) / 4);
+    cfg.blockDim = dim3(128);
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k_md_substep, a, k);
 }
 
 cudaError_t launch_md_diag(const AtomArgs &a, int *cell_of, int *neigh, cudaStream_t s) {
