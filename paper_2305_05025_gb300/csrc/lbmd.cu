@@ -30,6 +30,8 @@ constexpr int kCap = 64;   // atoms per bucket
 
 }  // namespace
 
+void lbmd::set_thread_error(const std::string &msg) { g_create_error = msg; }
+
 struct lbmd_s {
     lbmd_params p{};
     cudaStream_t stream = nullptr;            // caller's stream
@@ -191,6 +193,7 @@ void fill_physics(lbmd_t h) {
     for (int d = 0; d < 3; ++d) {
         A.nc[d] = h->na > 0 ? (int)std::floor((double)Ls[d] / (rc + p.skin)) : 3;
         A.fold[d] = A.nc[d] < kFold ? A.nc[d] : kFold;
+        A.fmask[d] = A.nc[d] <= kFold ? -1 : kFold - 1;
         A.Ld[d] = (double)Ls[d];
         A.hd[d] = (double)Ls[d] / A.nc[d];
         A.h[d] = (float)A.hd[d];
@@ -220,6 +223,7 @@ lbmd_status enqueue_step(lbmd_t h) {
     CK(h, cudaEventRecord(h->ev_join, h->s_lat));
     // Solute branch.
     if (h->na > 0) {
+        CK(h, launch_md_sort(h->A, h->s_main));
         CK(h, launch_interp(h->p.store, h->C, h->A, h->pop, h->s_main));
         for (int k = 0; k <= h->A.n_md; ++k) CK(h, launch_md_substep(h->A, k, h->s_main));
         CK(h, launch_spread(h->C, h->s_main));
@@ -388,7 +392,11 @@ lbmd_status lbmd_create(const lbmd_params *params, int n_atoms, const double *ma
             CREATE_TRY(dalloc_t(h, &A.count[g], B));
             CREATE_TRY(dalloc_t(h, &A.slot[g], B * A.cap));
             CREATE_TRY(dalloc_t(h, &A.bucket[g], (size_t)na));
+            CREATE_TRY(dalloc_t(h, &A.sidx[g], (size_t)na));
         }
+        CREATE_TRY(dalloc_t(h, &A.order, (size_t)na));
+        CREATE_TRY(dalloc_t(h, &A.scan_local, (size_t)64 * 64 * 64));
+        CREATE_TRY(dalloc_t(h, &A.scan_block, 256));
         // Topology: masses and a symmetric bond CSR.
         std::vector<float> m(na), im(na);
         for (int a = 0; a < na; ++a) {
@@ -487,6 +495,11 @@ lbmd_status lbmd_set_state(lbmd_t h, const float *f, const float *rho, const flo
             CK(h, cudaMemsetAsync(h->A.bucket[g], 0, h->na * sizeof(int), h->stream));
         }
         CK(h, cudaMemsetAsync(h->A.J, 0, na3 * sizeof(float), h->stream));
+        {
+            std::vector<int> ident(h->na);
+            for (int i = 0; i < h->na; ++i) ident[i] = i;
+            CK(h, cudaMemcpy(h->A.order, ident.data(), h->na * sizeof(int), cudaMemcpyHostToDevice));
+        }
         CK(h, cudaMemsetAsync(h->A.U, 0, na3 * sizeof(float), h->stream));
         CK(h, launch_md_prime(h->A, h->stream));
     }

@@ -8,6 +8,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <string>
+
 #include "../../include/lbmd.h"
 
 namespace lbmd {
@@ -203,7 +205,11 @@ struct AtomArgs {
     float *mass, *inv_m;
     const int *bstart, *bpart;  // bond CSR
     const float *bk, *br0;
-    int *count[3], *slot[3], *bucket[3];  // pair-search buckets by generation mod 3
+    int *count[3], *slot[3], *bucket[3], *sidx[3];  // pair-search buckets by generation mod 3
+    int fmask[3];         // bucket coordinate = cell & fmask (fold = nc, or 64 with mask 63)
+    int *order;           // atoms in warp-sorted (Morton bucket) order
+    int *scan_local;      // 64^3 Morton-code exclusive scan within blocks of 1024
+    int *scan_block;      // 256 block offsets
     DevState *ds;
 };
 
@@ -220,6 +226,9 @@ struct CouplingArgs {
     float4 *G;      // per node coupling force (x, y, z, unused)
     DevState *ds;
 };
+
+// Message returned by lbmd_last_error(NULL) on the calling thread.
+void set_thread_error(const std::string &msg);
 
 // Launchers (stream-ordered, no synchronisation).
 cudaError_t launch_lb_step(int store, const Lat &L, void *const buf[2], DevState *ds, cudaStream_t s);
@@ -238,6 +247,7 @@ cudaError_t launch_atom_momentum(const float *V, const float *mass, int na, doub
 cudaError_t launch_md_prime(const AtomArgs &a, cudaStream_t s);
 cudaError_t launch_md_substep(const AtomArgs &a, int k, cudaStream_t s);
 cudaError_t launch_md_diag(const AtomArgs &a, int *cell_of, int *neigh, cudaStream_t s);
+cudaError_t launch_md_sort(const AtomArgs &a, cudaStream_t s);
 
 cudaError_t launch_interp(int store, const CouplingArgs &c, const AtomArgs &a, void *const buf[2], cudaStream_t s);
 cudaError_t launch_spread(const CouplingArgs &c, cudaStream_t s);

@@ -2,19 +2,29 @@
 // bonds, and the velocity-Verlet substeps with Stokes friction (Sec. 2.2: the
 // atom receives gamma (u - v), u interpolated at the start of the coupled step).
 //
-// One kernel launch per substep, one thread per atom. Kernel k of a step
-// (k = 0..n_md) finishes substep k-1 (force at x_k, second half-kick) and
-// starts substep k (first half-kick, drift to x_{k+1}, insertion of the atom
-// into the buckets of generation k+1). Buckets rotate over three buffers by
-// generation g = step*n_md + k: kernel k reads g, fills g+1 and empties g-1.
+// One kernel launch per substep. Kernel k of a step (k = 0..n_md) finishes
+// substep k-1 (force at x_k, second half-kick) and starts substep k (first
+// half-kick, drift to x_{k+1}, insertion of the atom into the buckets of
+// generation k+1). Buckets rotate over three buffers by generation
+// g = step*n_md + k: kernel k reads g, fills g+1 and empties g-1.
+//
+// Warp-sorted cell list: at the start of every coupled step the atoms are
+// counting-sorted by bucket along a Morton curve of the bucket grid, so the 32
+// atoms of a warp sit in a compact block of cells. Each warp then stages the
+// candidates of its atoms' joint neighbourhood in shared memory once per
+// substep and every lane scans them for its own atom.
 #include "lbmd_internal.cuh"
 
 namespace lbmd {
 
 namespace {
 
+// c mod n for the usual case of c within one period of [0, n).
 __device__ __forceinline__ int wrapi(int c, int n) {
-    int r = c % n;
+    if ((unsigned)c < (unsigned)n) return c;
+    if (c < 0 && c >= -n) return c + n;
+    if (c >= n && c < 2 * n) return c - n;
+    const int r = c % n;
     return r < 0 ? r + n : r;
 }
 
@@ -90,8 +100,10 @@ __device__ __forceinline__ float bond_factor(const float dh[3], const float dl[3
     return -k * (diff / (r + r0)) / r;
 }
 
+// Bucket of a cell: cells fold onto a grid of at most 64 per axis (fold = nc
+// when nc <= 64, otherwise 64 and fmask = 63).
 __device__ __forceinline__ int bucket_of(const AtomArgs &A, const int c[3]) {
-    return ((c[2] % A.fold[2]) * A.fold[1] + (c[1] % A.fold[1])) * A.fold[0] + (c[0] % A.fold[0]);
+    return ((c[2] & A.fmask[2]) * A.fold[1] + (c[1] & A.fmask[1])) * A.fold[0] + (c[0] & A.fmask[0]);
 }
 
 // Current cell of an atom from its reference cell and FP32 offset.
@@ -200,6 +212,89 @@ __device__ __forceinline__ void insert(const AtomArgs &A, int g3, int a, const i
     else
         atomicOr(&A.ds->flags, FLAG_CELL);
     A.bucket[g3][a] = b;
+    A.sidx[g3][a] = s;
+}
+
+// ---------------------------------------------------------------------------
+// Warp-sorted order: counting sort of the atoms by bucket, buckets taken in
+// Morton order over a 64^3 grid (codes outside the bucket grid count zero).
+
+__device__ __forceinline__ unsigned spread3(unsigned v) {
+    unsigned r = 0;
+#pragma unroll
+    for (int i = 0; i < 6; ++i) r |= ((v >> i) & 1u) << (3 * i);
+    return r;
+}
+
+__device__ __forceinline__ unsigned morton3(int x, int y, int z) {
+    return spread3((unsigned)x) | (spread3((unsigned)y) << 1) | (spread3((unsigned)z) << 2);
+}
+
+__device__ __forceinline__ int compact3(unsigned m) {
+    int r = 0;
+#pragma unroll
+    for (int i = 0; i < 6; ++i) r |= (int)((m >> (3 * i)) & 1u) << i;
+    return r;
+}
+
+// Block-local exclusive scan of the bucket counts (1024 Morton codes per block).
+__global__ void __launch_bounds__(1024) k_sort_local(AtomArgs A) {
+    const int step = A.ds->step;
+    const int g3 = ((step % 3) * (A.n_md % 3)) % 3;
+    const unsigned m = blockIdx.x * 1024u + threadIdx.x;
+    const int x = compact3(m), y = compact3(m >> 1), z = compact3(m >> 2);
+    int cnt = 0;
+    if (x < A.fold[0] && y < A.fold[1] && z < A.fold[2]) cnt = A.count[g3][(z * A.fold[1] + y) * A.fold[0] + x];
+    __shared__ int wsum[32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int incl = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += t;
+    }
+    if (lane == 31) wsum[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+        int v = wsum[lane];
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int t = __shfl_up_sync(0xffffffffu, v, o);
+            if (lane >= o) v += t;
+        }
+        wsum[lane] = v;
+    }
+    __syncthreads();
+    const int before = warp ? wsum[warp - 1] : 0;
+    A.scan_local[m] = before + incl - cnt;
+    if (threadIdx.x == 1023) A.scan_block[blockIdx.x] = before + incl;
+}
+
+// Exclusive scan of the 256 block totals.
+__global__ void __launch_bounds__(256) k_sort_top(AtomArgs A) {
+    __shared__ int sh[256];
+    const int t = threadIdx.x;
+    sh[t] = A.scan_block[t];
+    __syncthreads();
+    for (int o = 1; o < 256; o <<= 1) {
+        const int v = t >= o ? sh[t - o] : 0;
+        __syncthreads();
+        sh[t] += v;
+        __syncthreads();
+    }
+    A.scan_block[t] = t ? sh[t - 1] : 0;
+}
+
+__global__ void __launch_bounds__(128) k_sort_scatter(AtomArgs A) {
+    const int a = blockIdx.x * blockDim.x + threadIdx.x;
+    if (a >= A.na) return;
+    const int step = A.ds->step;
+    const int g3 = ((step % 3) * (A.n_md % 3)) % 3;
+    const int b = A.bucket[g3][a];
+    const int x = b % A.fold[0], y = (b / A.fold[0]) % A.fold[1], z = b / (A.fold[0] * A.fold[1]);
+    const unsigned m = morton3(x, y, z);
+    const int pos = A.scan_block[m >> 10] + A.scan_local[m] + A.sidx[g3][a];
+    if (pos >= 0 && pos < A.na) A.order[pos] = a;
 }
 
 // Exact FP64 cell coordinate floor((x * nc) / L) mod nc.
@@ -251,27 +346,186 @@ __global__ void k_prime_force(AtomArgs A) {
         for (int d = 0; d < 3; ++d) A.F[d * A.na + a] = F[d];
 }
 
-// One warp per atom: the warp evaluates the force, lane 0 integrates.
+constexpr int TILE_CELLS = 256;  // cells of a warp's staged neighbourhood
+constexpr int TILE_CH = 128;     // candidates staged per chunk and warp
+constexpr int TILE_WARPS = 4;
+
+// Shifted-force LJ between lane atom a and candidate q (hi offsets already
+// within the cutoff test): refine the displacement with the lo parts, then
+// exclude bonded pairs.
+__device__ __forceinline__ void lj_pair(const AtomArgs &A, const float4 *__restrict__ Lq, int a, float4 pa, float4 la,
+                                        const int ca[3], int q, float4 pq, float f[3]) {
+    float dh[3], dl[3];
+    disp_df(A, pa, la, ca, pq, Lq[q], dh, dl);
+    const float d[3] = {dh[0] + dl[0], dh[1] + dl[1], dh[2] + dl[2]};
+    const float r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+    if (!(r2 < A.rc2f)) return;
+    if (bonded(A, a, q)) return;
+    const float inv_r2 = 1.0f / r2;
+    const float sr2 = A.lj_sig2 * inv_r2;
+    const float sr6 = sr2 * sr2 * sr2;
+    const float fr = A.lj_24eps * inv_r2 * sr6 * (2.f * sr6 - 1.f) - A.lj_fc * rsqrtf(r2);
+    f[0] += fr * d[0];
+    f[1] += fr * d[1];
+    f[2] += fr * d[2];
+}
+
+__device__ __forceinline__ float4 shfl4(float4 v, int src) {
+    return make_float4(__shfl_sync(0xffffffffu, v.x, src), __shfl_sync(0xffffffffu, v.y, src),
+                       __shfl_sync(0xffffffffu, v.z, src), __shfl_sync(0xffffffffu, v.w, src));
+}
+
+// Force on the 32 atoms of a warp (one per lane; invalid lanes take part in
+// the collective steps only). The box of cells within one cell of any of the
+// warp's atoms is enumerated, its bucket counts are prefix-summed into shared
+// memory, and the candidates are staged TILE_CH at a time; every lane then
+// scans each staged candidate against its own atom (broadcast reads). A warp
+// whose box is too large, or wider than the bucket fold (aliasing), falls back
+// to the per-atom search.
+__device__ void tile_force(const AtomArgs &A, const float4 *__restrict__ P, const float4 *__restrict__ Lq, int g3,
+                           bool valid, int a, float4 pa, float4 la, float F[3], int *s_cellb, int *s_cellp,
+                           float4 *s_P, int *s_q) {
+    const int lane = threadIdx.x & 31;
+    int ca[3], cc[3];
+    unpack_cref(pa.w, ca);
+    current_cell(A, pa, ca, cc);
+    int start[3], ext[3];
+    bool tile = true;
+    int ncell = 1;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        const int ref = __shfl_sync(0xffffffffu, cc[d], 0);
+        const int rel = wrapdiff(cc[d] - ref, A.nc[d]);
+        const int lo = __reduce_min_sync(0xffffffffu, valid ? rel : 0x3fffffff);
+        const int hi = __reduce_max_sync(0xffffffffu, valid ? rel : -0x3fffffff);
+        ext[d] = hi - lo + 3;
+        start[d] = ref + lo - 1;
+        if (ext[d] >= A.nc[d]) {
+            ext[d] = A.nc[d];
+            start[d] = 0;
+        }
+        if (ext[d] > A.fold[d]) tile = false;
+        ncell *= ext[d];
+    }
+    if (ncell > TILE_CELLS) tile = false;
+    float f[3] = {0.f, 0.f, 0.f};
+    if (!tile) {
+        for (int j = 0; j < 32; ++j) {
+            if (!__shfl_sync(0xffffffffu, (int)valid, j)) continue;
+            const int aj = __shfl_sync(0xffffffffu, a, j);
+            const float4 pj = shfl4(pa, j), lj = shfl4(la, j);
+            float Fj[3];
+            md_force_warp(A, P, Lq, g3, aj, pj, lj, Fj);
+            if (lane == j) {
+                F[0] = Fj[0];
+                F[1] = Fj[1];
+                F[2] = Fj[2];
+            }
+        }
+        return;
+    }
+    const int *__restrict__ cnt = A.count[g3];
+    const int *__restrict__ slots = A.slot[g3];
+    int total = 0;
+    for (int c0 = 0; c0 < ncell; c0 += 32) {
+        const int j = c0 + lane;
+        int b = 0, n = 0;
+        if (j < ncell) {
+            const int ix = j % ext[0], iy = (j / ext[0]) % ext[1], iz = j / (ext[0] * ext[1]);
+            const int c[3] = {wrapi(start[0] + ix, A.nc[0]), wrapi(start[1] + iy, A.nc[1]),
+                              wrapi(start[2] + iz, A.nc[2])};
+            b = bucket_of(A, c);
+            n = min(cnt[b], A.cap);
+        }
+        int incl = n;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int t = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += t;
+        }
+        if (j < ncell) {
+            s_cellb[j] = b;
+            s_cellp[j] = total + incl;
+        }
+        total += __shfl_sync(0xffffffffu, incl, 31);
+    }
+    __syncwarp();
+    for (int t0 = 0; t0 < total; t0 += TILE_CH) {
+        const int n = min(TILE_CH, total - t0);
+        for (int t = t0 + lane; t < t0 + n; t += 32) {
+            int lo = 0, hi = ncell - 1;  // first cell whose inclusive count exceeds t
+            while (lo < hi) {
+                const int mid = (lo + hi) >> 1;
+                if (s_cellp[mid] > t)
+                    hi = mid;
+                else
+                    lo = mid + 1;
+            }
+            const int before = lo ? s_cellp[lo - 1] : 0;
+            const int q = slots[(size_t)s_cellb[lo] * A.cap + (t - before)];
+            s_q[t - t0] = q;
+            s_P[t - t0] = P[q];
+        }
+        __syncwarp();
+        if (valid) {
+            for (int j = 0; j < n; ++j) {
+                const int q = s_q[j];
+                if (q == a) continue;
+                const float4 pq = s_P[j];
+                float d[3];
+                disp(A, pa, ca, pq, d);
+                if (d[0] * d[0] + d[1] * d[1] + d[2] * d[2] < A.rc2f * 1.0001f) lj_pair(A, Lq, a, pa, la, ca, q, pq, f);
+            }
+        }
+        __syncwarp();
+    }
+    if (valid) {
+        for (int s = A.bstart[a]; s < A.bstart[a + 1]; ++s) {
+            const int q = A.bpart[s];
+            float dh[3], dl[3];
+            disp_df(A, pa, la, ca, P[q], Lq[q], dh, dl);
+            const float fr = bond_factor(dh, dl, A.bk[s], A.br0[s]);
+            f[0] += fr * (dh[0] + dl[0]);
+            f[1] += fr * (dh[1] + dl[1]);
+            f[2] += fr * (dh[2] + dl[2]);
+        }
+    }
+    F[0] = f[0];
+    F[1] = f[1];
+    F[2] = f[2];
+}
+
+// One lane per atom in warp-sorted order: the warp evaluates the forces of its
+// 32 atoms together, then every lane integrates its own atom.
 __global__ void __launch_bounds__(128) k_md_substep(AtomArgs A, int k) {
     // With programmatic dependent launch this kernel may start before the
     // previous substep has finished: wait for its results first.
     cudaGridDependencySynchronize();
-    const int a = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    if (a >= A.na) return;
-    const long long gen = (long long)A.ds->step * A.n_md + k;
-    const int par = (int)(gen & 1);
-    const int g3 = (int)(gen % 3), gn3 = (int)((gen + 1) % 3), gp3 = (int)((gen + 2) % 3);
+    __shared__ int s_cellb[TILE_WARPS][TILE_CELLS];
+    __shared__ int s_cellp[TILE_WARPS][TILE_CELLS];
+    __shared__ float4 s_P[TILE_WARPS][TILE_CH];
+    __shared__ int s_q[TILE_WARPS][TILE_CH];
+    const int w = threadIdx.x >> 5;
+    const int na = A.na;
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (blockIdx.x * blockDim.x + w * 32 >= na) return;  // whole warp past the end
+    const bool valid = idx < na;
+    const int a = valid ? A.order[idx] : A.order[0];
+    const int step = A.ds->step;
+    const int g3 = ((step % 3) * (A.n_md % 3) + k) % 3;
+    const int gn3 = (g3 + 1) % 3, gp3 = (g3 + 2) % 3;
+    const int par = ((step & 1) * (A.n_md & 1) + k) & 1;
     const float4 pa = A.P[par][a];
     const float4 la = A.L[par][a];
-    const int na = A.na;
 
-    float F[3];
+    float F[3] = {0.f, 0.f, 0.f};
     if (k == 0) {
-        for (int d = 0; d < 3; ++d) F[d] = A.F[d * na + a];
+        if (valid)
+            for (int d = 0; d < 3; ++d) F[d] = A.F[d * na + a];
     } else {
-        md_force_warp(A, A.P[par], A.L[par], g3, a, pa, la, F);
+        tile_force(A, A.P[par], A.L[par], g3, valid, a, pa, la, F, s_cellb[w], s_cellp[w], s_P[w], s_q[w]);
     }
-    if ((threadIdx.x & 31) != 0) return;
+    if (!valid) return;
     float v[3], U[3], J[3];
     const float im = A.inv_m[a];
     for (int d = 0; d < 3; ++d) {
@@ -397,8 +651,8 @@ cudaError_t launch_md_prime(const AtomArgs &a, cudaStream_t s) {
 cudaError_t launch_md_substep(const AtomArgs &a, int k, cudaStream_t s) {
     if (a.na == 0) return cudaSuccess;
     cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3((a.na + 3) / 4);
-    cfg.blockDim = dim3(128);
+    cfg.gridDim = dim3((a.na + 32 * TILE_WARPS - 1) / (32 * TILE_WARPS));
+    cfg.blockDim = dim3(32 * TILE_WARPS);
     cfg.stream = s;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
@@ -406,6 +660,14 @@ cudaError_t launch_md_substep(const AtomArgs &a, int k, cudaStream_t s) {
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     return cudaLaunchKernelEx(&cfg, k_md_substep, a, k);
+}
+
+cudaError_t launch_md_sort(const AtomArgs &a, cudaStream_t s) {
+    if (a.na == 0) return cudaSuccess;
+    k_sort_local<<<256, 1024, 0, s>>>(a);
+    k_sort_top<<<1, 256, 0, s>>>(a);
+    k_sort_scatter<<<(a.na + 127) / 128, 128, 0, s>>>(a);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_md_diag(const AtomArgs &a, int *cell_of, int *neigh, cudaStream_t s) {
