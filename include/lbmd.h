@@ -181,6 +181,33 @@ void lbmd_destroy(lbmd_t h);
 /* ABI version, currently 1. */
 int lbmd_version(void);
 
+/* Largest lattice lbmd_fluid_sums_noalloc accepts: 65536 blocks of 256 nodes
+ * (256^3 nodes), the capacity of its fixed 2 MiB device scratch. */
+#define LBMD_NOALLOC_MAX_NODES 16777216
+
+/* Allocation-free FP64 fluid sums (the paper has no counterpart: a service of
+ * this library). For callers that cannot call cudaMalloc -- an engine or
+ * plugin host that reserves the device memory up front in its own pool and
+ * forbids allocations from outside it, or a time-critical loop that cannot
+ * afford the device synchronisation an allocation implies. No handle is
+ * needed and nothing is allocated: the per-block partial sums go to a
+ * file-scope device array of LBMD_NOALLOC_MAX_NODES/256 * 4 doubles that every
+ * GPU which loads the library keeps until the process exits.
+ *
+ * f: device pointer to FP32 populations in the ABI layout (19 * N SoA,
+ * N = nx*ny*nz <= LBMD_NOALLOC_MAX_NODES, larger sizes return LBMD_ERR_ARG).
+ * out: device pointer to 4 doubles, receives sum_n sum_i f_i and
+ * sum_n sum_i f_i c_i (x, y, z). Both stay owned by the caller. Enqueued on
+ * cuda_stream (NULL: the legacy default stream); asynchronous.
+ *
+ * The first call on a device (with that device current) looks up the
+ * device address of the scratch array; make that first call before any
+ * stream capture. All calls share the array and it keeps the last call's
+ * partials: calls that may overlap on the GPU (unordered streams) race and
+ * must be serialised by the caller. Errors: LBMD_ERR_ARG, LBMD_ERR_CUDA, with
+ * the message from lbmd_last_error(NULL). */
+lbmd_status lbmd_fluid_sums_noalloc(const float *f, int nx, int ny, int nz, double *out, void *cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif
