@@ -31,10 +31,10 @@ sys.path.insert(0, ROOT)
 from paper_2305_05025_gb300 import synth  # noqa: E402
 
 DEFAULT_WORKLOAD = "globule20k_lattice128"
-# Choices the workload description leaves open:
-# n_md resolves the LJ repulsion, gamma keeps the explicit friction exchange
-# stable once the globule is dense.
-DEFAULT_OVERRIDES = dict(n_md=128, gamma=0.05)
+# Choices the workload description leaves open: n_md resolves the LJ
+# repulsion, gamma keeps the explicit friction exchange stable once the
+# globule is dense, skin sets how long a neighbour list lasts.
+DEFAULT_OVERRIDES = dict(n_md=128, gamma=0.05, skin=0.3)
 METRIC = "coupled LB-MD MLUPS"
 
 

@@ -188,6 +188,8 @@ void fill_physics(lbmd_t h) {
     const double sr6 = std::pow(p.lj_sigma / rc, 6.0);
     A.lj_fc = (float)(24.0 * p.lj_eps * (2.0 * sr6 * sr6 - sr6) / rc);
     A.rc2f = (float)(rc * rc);
+    A.rl2 = (float)((rc + p.skin) * (rc + p.skin));
+    A.half_skin2 = (float)(0.25 * p.skin * p.skin);
     A.rc2d = rc * rc;
     const int Ls[3] = {p.nx, p.ny, p.nz};
     for (int d = 0; d < 3; ++d) {
@@ -395,6 +397,9 @@ lbmd_status lbmd_create(const lbmd_params *params, int n_atoms, const double *ma
             CREATE_TRY(dalloc_t(h, &A.sidx[g], (size_t)na));
         }
         CREATE_TRY(dalloc_t(h, &A.order, (size_t)na));
+        CREATE_TRY(dalloc_t(h, &A.nbr, (size_t)na * NL_MAX));
+        CREATE_TRY(dalloc_t(h, &A.nnb, (size_t)na));
+        CREATE_TRY(dalloc_t(h, &A.D, na3));
         CREATE_TRY(dalloc_t(h, &A.scan_local, (size_t)64 * 64 * 64));
         CREATE_TRY(dalloc_t(h, &A.scan_block, 256));
         // Topology: masses and a symmetric bond CSR.
@@ -499,6 +504,10 @@ lbmd_status lbmd_set_state(lbmd_t h, const float *f, const float *rho, const flo
             std::vector<int> ident(h->na);
             for (int i = 0; i < h->na; ++i) ident[i] = i;
             CK(h, cudaMemcpy(h->A.order, ident.data(), h->na * sizeof(int), cudaMemcpyHostToDevice));
+            CK(h, cudaMemsetAsync(h->A.nnb, 0, h->na * sizeof(int), h->stream));
+            CK(h, cudaMemsetAsync(h->A.D, 0, na3 * sizeof(float), h->stream));
+            const int one = 1;  // first force evaluation builds the lists
+            CK(h, cudaMemcpyAsync(&h->ds->nl_flag[0], &one, sizeof(int), cudaMemcpyHostToDevice, h->stream));
         }
         CK(h, cudaMemsetAsync(h->A.U, 0, na3 * sizeof(float), h->stream));
         CK(h, launch_md_prime(h->A, h->stream));

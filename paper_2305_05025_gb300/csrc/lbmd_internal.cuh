@@ -47,6 +47,7 @@ struct DevState {
     int n_touched;   // unique nodes claimed by atoms this step
     int flags;       // FLAG_* bits
     unsigned ticket; // last-block detection of the fix-up kernel
+    int nl_flag[3];  // neighbour-list rebuild requests, by generation mod 3
 };
 
 // Storage formats of the populations (delta f = f - w rho0 in every format).
@@ -183,6 +184,7 @@ __device__ __forceinline__ float node_velocity(const Lat &L, const float f[Q], c
 // relative error before its final rounding.
 
 constexpr int CREF_BITS = 10;  // cref packs three cell coordinates < 1024
+constexpr int NL_MAX = 256;    // neighbour-list capacity per atom (close packing of sigma = 0.4 beads within 1.3: ~200)
 
 struct AtomArgs {
     int na;
@@ -208,6 +210,11 @@ struct AtomArgs {
     int *count[3], *slot[3], *bucket[3], *sidx[3];  // pair-search buckets by generation mod 3
     int fmask[3];         // bucket coordinate = cell & fmask (fold = nc, or 64 with mask 63)
     int *order;           // atoms in warp-sorted (Morton bucket) order
+    int *nbr;             // na * NL_MAX neighbour lists (atom-major)
+    int *nnb;             // list lengths
+    float *D;             // 3*na drift since the last list build
+    float rl2;            // (rc + skin)^2, list radius squared
+    float half_skin2;     // (skin/2)^2, drift that triggers a rebuild
     int *scan_local;      // 64^3 Morton-code exclusive scan within blocks of 1024
     int *scan_block;      // 256 block offsets
     DevState *ds;

@@ -9,10 +9,9 @@
 // g = step*n_md + k: kernel k reads g, fills g+1 and empties g-1.
 //
 // Warp-sorted cell list: at the start of every coupled step the atoms are
-// counting-sorted by bucket along a Morton curve of the bucket grid, so the 32
-// atoms of a warp sit in a compact block of cells. Each warp then stages the
-// candidates of its atoms' joint neighbourhood in shared memory once per
-// substep and every lane scans them for its own atom.
+// counting-sorted by bucket along a Morton curve of the bucket grid; the
+// substep kernels visit atoms in that order, so neighbouring warps read
+// neighbouring atoms. Forces come from per-atom Verlet lists (see below).
 #include "lbmd_internal.cuh"
 
 namespace lbmd {
@@ -346,28 +345,112 @@ __global__ void k_prime_force(AtomArgs A) {
         for (int d = 0; d < 3; ++d) A.F[d * A.na + a] = F[d];
 }
 
-constexpr int TILE_CELLS = 256;  // cells of a warp's staged neighbourhood
-constexpr int TILE_CH = 128;     // candidates staged per chunk and warp
-constexpr int TILE_WARPS = 4;
+// ---------------------------------------------------------------------------
+// Verlet neighbour lists. Each atom keeps the non-bonded atoms within
+// rc + skin of it (at most NL_MAX). A list stays valid while no atom has
+// drifted more than skin/2 since it was built; the drift check raises a
+// device flag that makes the next force evaluation rebuild every list, from
+// the buckets of that generation, inside the same kernel. Flags rotate over
+// three slots like the buckets: kernel k reads slot g, raises g+1, clears g-1.
 
-// Shifted-force LJ between lane atom a and candidate q (hi offsets already
-// within the cutoff test): refine the displacement with the lo parts, then
-// exclude bonded pairs.
-__device__ __forceinline__ void lj_pair(const AtomArgs &A, const float4 *__restrict__ Lq, int a, float4 pa, float4 la,
-                                        const int ca[3], int q, float4 pq, float f[3]) {
-    float dh[3], dl[3];
-    disp_df(A, pa, la, ca, pq, Lq[q], dh, dl);
-    const float d[3] = {dh[0] + dl[0], dh[1] + dl[1], dh[2] + dl[2]};
-    const float r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
-    if (!(r2 < A.rc2f)) return;
-    if (bonded(A, a, q)) return;
-    const float inv_r2 = 1.0f / r2;
-    const float sr2 = A.lj_sig2 * inv_r2;
-    const float sr6 = sr2 * sr2 * sr2;
-    const float fr = A.lj_24eps * inv_r2 * sr6 * (2.f * sr6 - 1.f) - A.lj_fc * rsqrtf(r2);
-    f[0] += fr * d[0];
-    f[1] += fr * d[1];
-    f[2] += fr * d[2];
+// Builds atom a's list with the warp (27-cell search, ballot compaction).
+__device__ void build_list(const AtomArgs &A, const float4 *__restrict__ P, int g3, int a, float4 pa) {
+    const int lane = threadIdx.x & 31;
+    int ca[3], cc[3];
+    unpack_cref(pa.w, ca);
+    current_cell(A, pa, ca, cc);
+    int bucket = 0, n = 0;
+    if (lane < 27) {
+        const int ox = lane % 3 - 1, oy = (lane / 3) % 3 - 1, oz = lane / 9 - 1;
+        const int c[3] = {wrapi(cc[0] + ox, A.nc[0]), wrapi(cc[1] + oy, A.nc[1]), wrapi(cc[2] + oz, A.nc[2])};
+        bucket = bucket_of(A, c);
+        n = min(A.count[g3][bucket], A.cap);
+    }
+    int incl = n;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += t;
+    }
+    const int total = __shfl_sync(0xffffffffu, incl, 31);
+    int kept = 0;
+    int *__restrict__ out = A.nbr + (size_t)a * NL_MAX;
+    for (int t = lane; t - lane < total; t += 32) {
+        int pos = 0;
+#pragma unroll
+        for (int step = 16; step > 0; step >>= 1) {
+            const int probe = __shfl_sync(0xffffffffu, incl, pos + step - 1);
+            if (probe <= t) pos += step;
+        }
+        const int cb = __shfl_sync(0xffffffffu, bucket, pos & 31);
+        const int before = __shfl_sync(0xffffffffu, incl - n, pos & 31);
+        bool keep = false;
+        int q = 0;
+        if (t < total) {
+            q = A.slot[g3][(size_t)cb * A.cap + (t - before)];
+            if (q != a) {
+                float d[3];
+                disp(A, pa, ca, P[q], d);
+                keep = d[0] * d[0] + d[1] * d[1] + d[2] * d[2] < A.rl2 && !bonded(A, a, q);
+            }
+        }
+        const unsigned m = __ballot_sync(0xffffffffu, keep);
+        const int at = kept + __popc(m & ((1u << lane) - 1u));
+        if (keep && at < NL_MAX) out[at] = q;
+        kept += __popc(m);
+    }
+    if (lane == 0) {
+        A.nnb[a] = min(kept, NL_MAX);
+        if (kept > NL_MAX) atomicOr(&A.ds->flags, FLAG_CELL);
+    }
+    __syncwarp();
+}
+
+constexpr int TPA = 8;  // lanes per atom in the substep kernel
+
+// Conservative force on atom a from its list and its bonds, over the TPA
+// lanes of its group; every lane of the group returns the full force.
+__device__ void list_force(const AtomArgs &A, const float4 *__restrict__ P, const float4 *__restrict__ Lq, int a,
+                           float4 pa, float4 la, int sub, float F[3]) {
+    int ca[3];
+    unpack_cref(pa.w, ca);
+    float fx = 0.f, fy = 0.f, fz = 0.f;
+    const int nn = A.nnb[a];
+    const int *__restrict__ lst = A.nbr + (size_t)a * NL_MAX;
+    for (int j = sub; j < nn; j += TPA) {
+        const int q = lst[j];
+        float dh[3], dl[3];
+        disp_df(A, pa, la, ca, P[q], Lq[q], dh, dl);
+        const float d[3] = {dh[0] + dl[0], dh[1] + dl[1], dh[2] + dl[2]};
+        const float r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+        if (r2 < A.rc2f) {
+            const float inv_r2 = 1.0f / r2;
+            const float sr2 = A.lj_sig2 * inv_r2;
+            const float sr6 = sr2 * sr2 * sr2;
+            const float fr = A.lj_24eps * inv_r2 * sr6 * (2.f * sr6 - 1.f) - A.lj_fc * rsqrtf(r2);
+            fx += fr * d[0];
+            fy += fr * d[1];
+            fz += fr * d[2];
+        }
+    }
+    for (int s = A.bstart[a] + sub; s < A.bstart[a + 1]; s += TPA) {
+        const int q = A.bpart[s];
+        float dh[3], dl[3];
+        disp_df(A, pa, la, ca, P[q], Lq[q], dh, dl);
+        const float fr = bond_factor(dh, dl, A.bk[s], A.br0[s]);
+        fx += fr * (dh[0] + dl[0]);
+        fy += fr * (dh[1] + dl[1]);
+        fz += fr * (dh[2] + dl[2]);
+    }
+#pragma unroll
+    for (int o = TPA / 2; o > 0; o >>= 1) {
+        fx += __shfl_xor_sync(0xffffffffu, fx, o);
+        fy += __shfl_xor_sync(0xffffffffu, fy, o);
+        fz += __shfl_xor_sync(0xffffffffu, fz, o);
+    }
+    F[0] = fx;
+    F[1] = fy;
+    F[2] = fz;
 }
 
 __device__ __forceinline__ float4 shfl4(float4 v, int src) {
@@ -375,212 +458,116 @@ __device__ __forceinline__ float4 shfl4(float4 v, int src) {
                        __shfl_sync(0xffffffffu, v.z, src), __shfl_sync(0xffffffffu, v.w, src));
 }
 
-// Force on the 32 atoms of a warp (one per lane; invalid lanes take part in
-// the collective steps only). The box of cells within one cell of any of the
-// warp's atoms is enumerated, its bucket counts are prefix-summed into shared
-// memory, and the candidates are staged TILE_CH at a time; every lane then
-// scans each staged candidate against its own atom (broadcast reads). A warp
-// whose box is too large, or wider than the bucket fold (aliasing), falls back
-// to the per-atom search.
-__device__ void tile_force(const AtomArgs &A, const float4 *__restrict__ P, const float4 *__restrict__ Lq, int g3,
-                           bool valid, int a, float4 pa, float4 la, float F[3], int *s_cellb, int *s_cellp,
-                           float4 *s_P, int *s_q) {
-    const int lane = threadIdx.x & 31;
-    int ca[3], cc[3];
-    unpack_cref(pa.w, ca);
-    current_cell(A, pa, ca, cc);
-    int start[3], ext[3];
-    bool tile = true;
-    int ncell = 1;
-#pragma unroll
-    for (int d = 0; d < 3; ++d) {
-        const int ref = __shfl_sync(0xffffffffu, cc[d], 0);
-        const int rel = wrapdiff(cc[d] - ref, A.nc[d]);
-        const int lo = __reduce_min_sync(0xffffffffu, valid ? rel : 0x3fffffff);
-        const int hi = __reduce_max_sync(0xffffffffu, valid ? rel : -0x3fffffff);
-        ext[d] = hi - lo + 3;
-        start[d] = ref + lo - 1;
-        if (ext[d] >= A.nc[d]) {
-            ext[d] = A.nc[d];
-            start[d] = 0;
-        }
-        if (ext[d] > A.fold[d]) tile = false;
-        ncell *= ext[d];
-    }
-    if (ncell > TILE_CELLS) tile = false;
-    float f[3] = {0.f, 0.f, 0.f};
-    if (!tile) {
-        for (int j = 0; j < 32; ++j) {
-            if (!__shfl_sync(0xffffffffu, (int)valid, j)) continue;
-            const int aj = __shfl_sync(0xffffffffu, a, j);
-            const float4 pj = shfl4(pa, j), lj = shfl4(la, j);
-            float Fj[3];
-            md_force_warp(A, P, Lq, g3, aj, pj, lj, Fj);
-            if (lane == j) {
-                F[0] = Fj[0];
-                F[1] = Fj[1];
-                F[2] = Fj[2];
-            }
-        }
-        return;
-    }
-    const int *__restrict__ cnt = A.count[g3];
-    const int *__restrict__ slots = A.slot[g3];
-    int total = 0;
-    for (int c0 = 0; c0 < ncell; c0 += 32) {
-        const int j = c0 + lane;
-        int b = 0, n = 0;
-        if (j < ncell) {
-            const int ix = j % ext[0], iy = (j / ext[0]) % ext[1], iz = j / (ext[0] * ext[1]);
-            const int c[3] = {wrapi(start[0] + ix, A.nc[0]), wrapi(start[1] + iy, A.nc[1]),
-                              wrapi(start[2] + iz, A.nc[2])};
-            b = bucket_of(A, c);
-            n = min(cnt[b], A.cap);
-        }
-        int incl = n;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const int t = __shfl_up_sync(0xffffffffu, incl, o);
-            if (lane >= o) incl += t;
-        }
-        if (j < ncell) {
-            s_cellb[j] = b;
-            s_cellp[j] = total + incl;
-        }
-        total += __shfl_sync(0xffffffffu, incl, 31);
-    }
-    __syncwarp();
-    for (int t0 = 0; t0 < total; t0 += TILE_CH) {
-        const int n = min(TILE_CH, total - t0);
-        for (int t = t0 + lane; t < t0 + n; t += 32) {
-            int lo = 0, hi = ncell - 1;  // first cell whose inclusive count exceeds t
-            while (lo < hi) {
-                const int mid = (lo + hi) >> 1;
-                if (s_cellp[mid] > t)
-                    hi = mid;
-                else
-                    lo = mid + 1;
-            }
-            const int before = lo ? s_cellp[lo - 1] : 0;
-            const int q = slots[(size_t)s_cellb[lo] * A.cap + (t - before)];
-            s_q[t - t0] = q;
-            s_P[t - t0] = P[q];
-        }
-        __syncwarp();
-        if (valid) {
-            for (int j = 0; j < n; ++j) {
-                const int q = s_q[j];
-                if (q == a) continue;
-                const float4 pq = s_P[j];
-                float d[3];
-                disp(A, pa, ca, pq, d);
-                if (d[0] * d[0] + d[1] * d[1] + d[2] * d[2] < A.rc2f * 1.0001f) lj_pair(A, Lq, a, pa, la, ca, q, pq, f);
-            }
-        }
-        __syncwarp();
-    }
-    if (valid) {
-        for (int s = A.bstart[a]; s < A.bstart[a + 1]; ++s) {
-            const int q = A.bpart[s];
-            float dh[3], dl[3];
-            disp_df(A, pa, la, ca, P[q], Lq[q], dh, dl);
-            const float fr = bond_factor(dh, dl, A.bk[s], A.br0[s]);
-            f[0] += fr * (dh[0] + dl[0]);
-            f[1] += fr * (dh[1] + dl[1]);
-            f[2] += fr * (dh[2] + dl[2]);
-        }
-    }
-    F[0] = f[0];
-    F[1] = f[1];
-    F[2] = f[2];
-}
-
-// One lane per atom in warp-sorted order: the warp evaluates the forces of its
-// 32 atoms together, then every lane integrates its own atom.
+// TPA lanes per atom, atoms in warp-sorted order (neighbouring warps touch
+// neighbouring atoms). When the flag of this generation is up the warp first
+// rebuilds the lists of its atoms one after the other (all 32 lanes on each);
+// then each group evaluates its atom's force over the list, lanes 0-2 of the
+// group integrate one component each, and lane 0 re-bins the atom.
 __global__ void __launch_bounds__(128) k_md_substep(AtomArgs A, int k) {
     // With programmatic dependent launch this kernel may start before the
     // previous substep has finished: wait for its results first.
     cudaGridDependencySynchronize();
-    __shared__ int s_cellb[TILE_WARPS][TILE_CELLS];
-    __shared__ int s_cellp[TILE_WARPS][TILE_CELLS];
-    __shared__ float4 s_P[TILE_WARPS][TILE_CH];
-    __shared__ int s_q[TILE_WARPS][TILE_CH];
-    const int w = threadIdx.x >> 5;
+    const int lane = threadIdx.x & 31;
+    const int sub = lane & (TPA - 1);
+    const int slot = ((blockIdx.x * blockDim.x + threadIdx.x) >> 5) * (32 / TPA) + lane / TPA;
     const int na = A.na;
-    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
-    if (blockIdx.x * blockDim.x + w * 32 >= na) return;  // whole warp past the end
-    const bool valid = idx < na;
-    const int a = valid ? A.order[idx] : A.order[0];
     const int step = A.ds->step;
     const int g3 = ((step % 3) * (A.n_md % 3) + k) % 3;
     const int gn3 = (g3 + 1) % 3, gp3 = (g3 + 2) % 3;
     const int par = ((step & 1) * (A.n_md & 1) + k) & 1;
+    const int rebuild = A.ds->nl_flag[g3];
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        A.ds->nl_flag[gp3] = 0;
+        // Kernel 0 evaluates no force: hand a pending rebuild on to kernel 1.
+        if (k == 0 && rebuild) atomicOr(&A.ds->nl_flag[gn3], 1);
+    }
+    const int warp_first = slot - lane / TPA;
+    if (warp_first >= na) return;  // whole warp past the end
+    const bool valid = slot < na;
+    const int a = A.order[valid ? slot : warp_first];
+    // Issue the integration loads early: lane d < 3 of the group owns
+    // component d.
+    const int dcomp = sub < 3 ? sub : 0;
+    const float vd = A.V[dcomp * na + a], Ud = A.U[dcomp * na + a];
+    const float Jd = k == 0 ? 0.f : A.J[dcomp * na + a];
+    const float im = A.inv_m[a];
     const float4 pa = A.P[par][a];
     const float4 la = A.L[par][a];
-
-    float F[3] = {0.f, 0.f, 0.f};
+    float F[3];
     if (k == 0) {
-        if (valid)
-            for (int d = 0; d < 3; ++d) F[d] = A.F[d * na + a];
+        F[0] = A.F[a];
+        F[1] = A.F[na + a];
+        F[2] = A.F[2 * na + a];
     } else {
-        tile_force(A, A.P[par], A.L[par], g3, valid, a, pa, la, F, s_cellb[w], s_cellp[w], s_P[w], s_q[w]);
+        if (rebuild) {
+            for (int g = 0; g < 32 / TPA; ++g) {
+                const int ag = __shfl_sync(0xffffffffu, a, g * TPA);
+                const int vg = __shfl_sync(0xffffffffu, (int)valid, g * TPA);
+                const float4 pg = shfl4(pa, g * TPA);
+                if (vg) build_list(A, A.P[par], g3, ag, pg);
+            }
+            if (valid && sub < 3) A.D[sub * na + a] = 0.f;
+            __syncwarp();
+        }
+        list_force(A, A.P[par], A.L[par], a, pa, la, sub, F);
     }
     if (!valid) return;
-    float v[3], U[3], J[3];
-    const float im = A.inv_m[a];
-    for (int d = 0; d < 3; ++d) {
-        v[d] = A.V[d * na + a];
-        U[d] = A.U[d * na + a];
-        J[d] = k == 0 ? 0.f : A.J[d * na + a];
-    }
-    if (k > 0) {  // second half-kick of substep k-1, drag at v_{k-1/2}
-        for (int d = 0; d < 3; ++d) {
-            const float drag = A.gamma * (U[d] - v[d]);
-            J[d] += A.hdt * drag;
-            v[d] += A.hdt * (F[d] + drag) * im;
+    // Lanes 0-2: one velocity-Verlet component each.
+    float v = vd, J = Jd, p = 0.f, lo = 0.f, Dd = 0.f;
+    const float Fd = sub == 0 ? F[0] : (sub == 1 ? F[1] : F[2]);
+    if (sub < 3) {
+        if (k > 0) {  // second half-kick of substep k-1, drag at v_{k-1/2}
+            const float drag = A.gamma * (Ud - v);
+            J += A.hdt * drag;
+            v += A.hdt * (Fd + drag) * im;
         }
-    }
-    if (k < A.n_md) {  // first half-kick of substep k, drag at v_k, then drift
-        for (int d = 0; d < 3; ++d) {
-            const float drag = A.gamma * (U[d] - v[d]);
-            J[d] += A.hdt * drag;
-            v[d] += A.hdt * (F[d] + drag) * im;
-        }
-        float p[3] = {pa.x, pa.y, pa.z}, lo[3] = {la.x, la.y, la.z};
-        for (int d = 0; d < 3; ++d) {
+        if (k < A.n_md) {  // first half-kick of substep k, drag at v_k, then drift
+            const float drag = A.gamma * (Ud - v);
+            J += A.hdt * drag;
+            v += A.hdt * (Fd + drag) * im;
+            p = sub == 0 ? pa.x : (sub == 1 ? pa.y : pa.z);
+            lo = sub == 0 ? la.x : (sub == 1 ? la.y : la.z);
             // Error-free update of hi + lo by v dt (two-sum plus the exact
             // product error).
-            const float inc = v[d] * A.dt;
-            const float e_mul = fmaf(v[d], A.dt, -inc);
+            const float inc = v * A.dt;
+            const float e_mul = fmaf(v, A.dt, -inc);
             float s, e_add;
-            two_sum(p[d], inc, s, e_add);
-            p[d] = s;
-            lo[d] += e_add + e_mul;
+            two_sum(p, inc, s, e_add);
+            p = s;
+            lo += e_add + e_mul;
+            Dd = A.D[sub * na + a] + inc;
+            A.D[sub * na + a] = Dd;
+        } else {
+            // End of the coupled step: cache the force and advance the FP64
+            // accumulator by the compensated displacement.
+            const float pc = sub == 0 ? pa.x : (sub == 1 ? pa.y : pa.z);
+            const float lc = sub == 0 ? la.x : (sub == 1 ? la.y : la.z);
+            A.F[sub * na + a] = Fd;
+            A.X[sub * na + a] += ((double)pc - (double)A.P0[sub * na + a]) + ((double)lc - (double)A.R0[sub * na + a]);
         }
-        const float4 pn = make_float4(p[0], p[1], p[2], pa.w);
-        A.P[par ^ 1][a] = pn;
-        A.L[par ^ 1][a] = make_float4(lo[0], lo[1], lo[2], 0.f);
-        A.count[gp3][A.bucket[gp3][a]] = 0;
-        int cr[3], c[3];
-        unpack_cref(pa.w, cr);
-        current_cell(A, pn, cr, c);
-        insert(A, gn3, a, c);
-        if (!(isfinite(p[0]) && isfinite(p[1]) && isfinite(p[2]))) atomicOr(&A.ds->flags, FLAG_NONFINITE);
-    } else {
-        // End of the coupled step: cache the force and advance the FP64
-        // accumulator by the compensated displacement.
-        const float pc[3] = {pa.x, pa.y, pa.z}, lc[3] = {la.x, la.y, la.z};
-        for (int d = 0; d < 3; ++d) {
-            A.F[d * na + a] = F[d];
-            const double disp64 = ((double)pc[d] - (double)A.P0[d * na + a]) +
-                                  ((double)lc[d] - (double)A.R0[d * na + a]);
-            A.X[d * na + a] += disp64;
-        }
+        A.V[sub * na + a] = v;
+        A.J[sub * na + a] = J;
     }
-    for (int d = 0; d < 3; ++d) {
-        A.V[d * na + a] = v[d];
-        A.J[d * na + a] = J[d];
-    }
+    if (k == A.n_md) return;
+    const int base = lane & ~(TPA - 1);
+    const unsigned gm = 0xffu << base;  // this group's lanes (valid groups are whole)
+    const float px = __shfl_sync(gm, p, base), py = __shfl_sync(gm, p, base + 1), pz = __shfl_sync(gm, p, base + 2);
+    const float lx = __shfl_sync(gm, lo, base), ly = __shfl_sync(gm, lo, base + 1), lz = __shfl_sync(gm, lo, base + 2);
+    const float D2 = __shfl_sync(gm, Dd * Dd, base) + __shfl_sync(gm, Dd * Dd, base + 1) +
+                     __shfl_sync(gm, Dd * Dd, base + 2);
+    if (sub != 0) return;
+    const float4 pn = make_float4(px, py, pz, pa.w);
+    A.P[par ^ 1][a] = pn;
+    A.L[par ^ 1][a] = make_float4(lx, ly, lz, 0.f);
+    A.count[gp3][A.bucket[gp3][a]] = 0;
+    int cr[3], c[3];
+    unpack_cref(pa.w, cr);
+    current_cell(A, pn, cr, c);
+    insert(A, gn3, a, c);
+    if (!(isfinite(px) && isfinite(py) && isfinite(pz))) atomicOr(&A.ds->flags, FLAG_NONFINITE);
+    // Drift since the last list build: past half the skin a pair may have
+    // entered the cutoff unseen, so the next force rebuilds.
+    if (!(D2 <= A.half_skin2)) atomicOr(&A.ds->nl_flag[gn3], 1);
 }
 
 // Diagnostics: exact FP64 cells and neighbour counts (strict r^2 < rc^2,
@@ -651,8 +638,8 @@ cudaError_t launch_md_prime(const AtomArgs &a, cudaStream_t s) {
 cudaError_t launch_md_substep(const AtomArgs &a, int k, cudaStream_t s) {
     if (a.na == 0) return cudaSuccess;
     cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3((a.na + 32 * TILE_WARPS - 1) / (32 * TILE_WARPS));
-    cfg.blockDim = dim3(32 * TILE_WARPS);
+    cfg.gridDim = dim3((a.na + 4 * (32 / TPA) - 1) / (4 * (32 / TPA)));  // TPA lanes per atom
+    cfg.blockDim = dim3(128);
     cfg.stream = s;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;

@@ -42,8 +42,10 @@ def test_cell_membership_and_neighbour_counts_bit_exact(orc, c1):
     assert np.array_equal(neigh, orc.neighbour_counts(cfg, inp["x"]))
 
 
-def test_cell_list_after_steps_matches_oracle_on_gpu_positions(orc, c1):
+@pytest.mark.parametrize("skin", [0.0, 0.3])
+def test_cell_list_after_steps_matches_oracle_on_gpu_positions(orc, c1, skin):
     cfg, inp = c1
+    cfg = dict(cfg, skin=skin)
     h = make(dict(cfg, gamma=0.05), inp)
     lbmd.lbmd_step(h, 3)
     x = lbmd.lbmd_get_fields(h, x=True)["x"]
@@ -98,11 +100,14 @@ def _teacher_forced(orc, cfg, inp, steps):
         for k in worst:
             worst[k] = max(worst[k], errs[k] / max(1e-5, np.sqrt(cfg["n_md"]) * floors[k]))
         done += 1
+    lbmd.lbmd_check(h)  # no bucket or neighbour-list overflow, no non-finite value
     return worst, done
 
 
-def test_one_coupled_step_matches_oracle(orc, c1):
+@pytest.mark.parametrize("skin", [0.0, 0.3])
+def test_one_coupled_step_matches_oracle(orc, c1, skin):
     cfg, inp = c1
+    cfg = dict(cfg, skin=skin)
     h = make(cfg, inp)
     f, x, v, topo = oracle_start(orc, cfg, inp)
     lbmd.lbmd_step(h, 1)
@@ -123,7 +128,7 @@ def test_teacher_forced_100_steps_chain500(orc, c1):
     exchange stable once the chain is dense (gamma = 0.5 diverges near step
     20, in the oracle too)."""
     cfg, inp = c1
-    worst, done = _teacher_forced(orc, dict(cfg, gamma=0.05), inp, 100)
+    worst, done = _teacher_forced(orc, dict(cfg, gamma=0.05, skin=0.3), inp, 100)
     assert done == 100
     print("teacher-forced worst error / bound:", worst)
     for k, r in worst.items():
@@ -139,11 +144,12 @@ def test_teacher_forced_literal_gamma(orc, c1):
         assert r <= 1.0, (k, r)
 
 
-def test_free_running_harmonic_chain_100_steps(orc):
+@pytest.mark.parametrize("skin", [0.0, 0.3])
+def test_free_running_harmonic_chain_100_steps(orc, skin):
     """Without Lennard-Jones (eps = 0) the chain is a damped harmonic network
     coupled to the fluid: not chaotic, so free-running FP32 and FP64
     trajectories stay together over 100 steps."""
-    cfg = synth.workload("chain500_lattice32", n_md=128, lj_eps=0.0, gamma=0.5, nx=24, ny=20, nz=28)
+    cfg = synth.workload("chain500_lattice32", n_md=128, lj_eps=0.0, gamma=0.5, nx=24, ny=20, nz=28, skin=skin)
     inp = synth.inputs(cfg, 2)
     rng = np.random.default_rng(3)
     inp["v"] = 0.05 * rng.standard_normal(inp["v"].shape)
