@@ -40,7 +40,7 @@ __global__ void __launch_bounds__(256) k_lb_step(Lat L, typename Store<S>::T *b0
 // last block to finish advances the step counter and empties the list.
 template <int S>
 __global__ void __launch_bounds__(256) k_lb_fix(Lat L, typename Store<S>::T *b0, typename Store<S>::T *b1,
-                                                const int *touched, int cap, float4 *G, DevState *ds) {
+                                                const int *touched, int cap, float4 *G, DevState *ds, int keep) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const int cnt = min(ds->n_touched, cap);
     const int step = ds->step;
@@ -62,7 +62,7 @@ __global__ void __launch_bounds__(256) k_lb_fix(Lat L, typename Store<S>::T *b0,
         if (!isfinite(rho)) atomicOr(&ds->flags, FLAG_NONFINITE);
 #pragma unroll
         for (int q = 0; q < Q; ++q) Store<S>::st_plain(dst + (size_t)q * L.N + node, f[q]);
-        G[node] = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (!keep) G[node] = make_float4(0.f, 0.f, 0.f, 0.f);
     }
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -70,7 +70,7 @@ __global__ void __launch_bounds__(256) k_lb_fix(Lat L, typename Store<S>::T *b0,
         const unsigned t = atomicAdd(&ds->ticket, 1u);
         if (t == gridDim.x - 1) {
             ds->step = step + 1;
-            ds->n_touched = 0;
+            if (!keep) ds->n_touched = 0;
             ds->ticket = 0;
             __threadfence();
         }
@@ -264,7 +264,7 @@ cudaError_t launch_lb_step(int store, const Lat &L, void *const buf[2], DevState
 cudaError_t launch_lb_fix(int store, const Lat &L, void *const buf[2], const CouplingArgs &c, int grid,
                           cudaStream_t s) {
     LBMD_DISPATCH(store, (k_lb_fix<SV><<<grid, 256, 0, s>>>(L, (T *)buf[0], (T *)buf[1], c.touched, c.touched_cap,
-                                                             c.G, c.ds)));
+                                                             c.G, c.ds, c.keep)));
     return cudaGetLastError();
 }
 

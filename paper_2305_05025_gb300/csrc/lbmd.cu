@@ -57,6 +57,20 @@ struct lbmd_s {
     int alloc_count = 0;
     void *stage = nullptr;  // device staging for host-pointer set/get (lazily sized)
     size_t stage_bytes = 0;
+    int *ident = nullptr;   // identity atom order
+    // lbmd_backward buffers (allocated on first use, sized for its arguments)
+    std::vector<void *> adj_allocs;
+    int adj_ckpts = 0, adj_seg = 0;
+    void *ck_lat = nullptr, *seg_lat = nullptr;
+    double *ck_X = nullptr, *seg_X = nullptr;
+    float *ck_V = nullptr, *seg_V = nullptr, *ck_F = nullptr, *seg_F = nullptr;
+    float4 *recP = nullptr, *recL = nullptr;
+    float *recV = nullptr, *recF = nullptr;
+    float *hat[2] = {nullptr, nullptr};
+    AdjArgs D{};
+    int *adj_count = nullptr, *adj_slot = nullptr;
+    double *obs_acc = nullptr;  // [0] sum, [1..7] scratch
+    int adj_blocks = 0;
 };
 
 namespace {
@@ -303,6 +317,128 @@ cudaError_t stage(lbmd_t h, size_t bytes, void **out) {
     return cudaSuccess;
 }
 
+// ---------------------------------------------------------------------------
+// lbmd_backward support: checkpoints of the raw state, restore, and the
+// recording re-run of one step.
+
+lbmd_status adj_alloc(lbmd_t h, void **p, size_t bytes) {
+    cudaError_t e = cudaMalloc(p, bytes < 16 ? 16 : bytes);
+    if (e != cudaSuccess) return cuda_fail(h, e, "cudaMalloc (adjoint)");
+    h->adj_allocs.push_back(*p);
+    return LBMD_OK;
+}
+
+lbmd_status adj_prepare(lbmd_t h, int n_steps, int K) {
+    const int nseg = (n_steps + K - 1) / K;
+    if (h->adj_ckpts >= nseg + 1 && h->adj_seg >= K) return LBMD_OK;
+    for (void *p : h->adj_allocs) cudaFree(p);
+    h->adj_allocs.clear();
+    const size_t N = h->L.N, na = (size_t)h->na, na3 = 3 * na, nm = (size_t)h->A.n_md + 1;
+    const size_t lat = N * Q * store_bytes(h->p.store);
+    void *p;
+    const int C = nseg + 1;
+    TRY(adj_alloc(h, &h->ck_lat, lat * C));
+    TRY(adj_alloc(h, &p, na3 * sizeof(double) * C)); h->ck_X = (double *)p;
+    TRY(adj_alloc(h, &p, na3 * sizeof(float) * C)); h->ck_V = (float *)p;
+    TRY(adj_alloc(h, &p, na3 * sizeof(float) * C)); h->ck_F = (float *)p;
+    TRY(adj_alloc(h, &h->seg_lat, lat * K));
+    TRY(adj_alloc(h, &p, na3 * sizeof(double) * K)); h->seg_X = (double *)p;
+    TRY(adj_alloc(h, &p, na3 * sizeof(float) * K)); h->seg_V = (float *)p;
+    TRY(adj_alloc(h, &p, na3 * sizeof(float) * K)); h->seg_F = (float *)p;
+    TRY(adj_alloc(h, &p, nm * na * sizeof(float4))); h->recP = (float4 *)p;
+    TRY(adj_alloc(h, &p, nm * na * sizeof(float4))); h->recL = (float4 *)p;
+    TRY(adj_alloc(h, &p, nm * na3 * sizeof(float))); h->recV = (float *)p;
+    TRY(adj_alloc(h, &p, nm * na3 * sizeof(float))); h->recF = (float *)p;
+    TRY(adj_alloc(h, &p, N * Q * sizeof(float))); h->hat[0] = (float *)p;
+    TRY(adj_alloc(h, &p, N * Q * sizeof(float))); h->hat[1] = (float *)p;
+    AdjArgs &D = h->D;
+    TRY(adj_alloc(h, &p, N * sizeof(float4))); D.Ghat = (float4 *)p;
+    TRY(adj_alloc(h, &p, N * sizeof(float4))); D.Uhat = (float4 *)p;
+    float **arrs[6] = {&D.xhat, &D.vhat, &D.p, &D.Jhat, &D.Uat_hat, &D.xw};
+    for (float **a : arrs) {
+        TRY(adj_alloc(h, &p, na3 * sizeof(float)));
+        *a = (float *)p;
+    }
+    TRY(adj_alloc(h, &p, na * sizeof(double))); D.gam_acc = (double *)p;
+    TRY(adj_alloc(h, &p, 2 * sizeof(double))); D.par_acc = (double *)p;
+    h->adj_blocks = adj_lb_blocks(h->L);
+    TRY(adj_alloc(h, &p, 2 * (size_t)h->adj_blocks * sizeof(double))); D.partials = (double *)p;
+    const size_t B = (size_t)h->A.fold[0] * h->A.fold[1] * h->A.fold[2];
+    TRY(adj_alloc(h, &p, B * sizeof(int))); h->adj_count = (int *)p;
+    TRY(adj_alloc(h, &p, B * h->A.cap * sizeof(int))); h->adj_slot = (int *)p;
+    TRY(adj_alloc(h, &p, 8 * sizeof(double))); h->obs_acc = (double *)p;
+    h->adj_ckpts = C;
+    h->adj_seg = K;
+    return LBMD_OK;
+}
+
+// Saves the raw state (current storage buffer, X, V, cached F) into slot i of
+// the checkpoints (ck = true) or of the segment store.
+lbmd_status adj_save(lbmd_t h, int i, bool ck) {
+    const size_t N = h->L.N, na3 = 3 * (size_t)h->na;
+    const size_t lat = N * Q * store_bytes(h->p.store);
+    char *L = (char *)(ck ? h->ck_lat : h->seg_lat) + lat * i;
+    cudaStream_t s = h->stream;
+    CK(h, cudaMemcpyAsync(L, h->pop[h->steps & 1], lat, cudaMemcpyDeviceToDevice, s));
+    CK(h, cudaMemcpyAsync((ck ? h->ck_X : h->seg_X) + na3 * i, h->A.X, na3 * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    CK(h, cudaMemcpyAsync((ck ? h->ck_V : h->seg_V) + na3 * i, h->A.V, na3 * sizeof(float), cudaMemcpyDeviceToDevice, s));
+    CK(h, cudaMemcpyAsync((ck ? h->ck_F : h->seg_F) + na3 * i, h->A.F, na3 * sizeof(float), cudaMemcpyDeviceToDevice, s));
+    return LBMD_OK;
+}
+
+// Restores slot i as the current state, step counter 0 (buffer 0), with fresh
+// buckets, touched tags and neighbour lists, and the saved cached force.
+lbmd_status adj_restore(lbmd_t h, int i, bool ck) {
+    const size_t N = h->L.N, na = (size_t)h->na, na3 = 3 * na;
+    const size_t lat = N * Q * store_bytes(h->p.store);
+    cudaStream_t s = h->stream;
+    const char *L = (const char *)(ck ? h->ck_lat : h->seg_lat) + lat * i;
+    CK(h, cudaMemcpyAsync(h->pop[0], L, lat, cudaMemcpyDeviceToDevice, s));
+    CK(h, cudaMemsetAsync(h->ds, 0, sizeof(DevState), s));
+    const int one = 1;
+    CK(h, cudaMemcpyAsync(&h->ds->nl_flag[0], &one, sizeof(int), cudaMemcpyHostToDevice, s));
+    CK(h, cudaMemsetAsync(h->C.tag, 0, N * sizeof(int), s));
+    CK(h, cudaMemsetAsync(h->C.G, 0, N * sizeof(float4), s));
+    CK(h, cudaMemcpyAsync(h->A.X, (ck ? h->ck_X : h->seg_X) + na3 * i, na3 * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    CK(h, cudaMemcpyAsync(h->A.V, (ck ? h->ck_V : h->seg_V) + na3 * i, na3 * sizeof(float), cudaMemcpyDeviceToDevice, s));
+    const size_t B = (size_t)h->A.fold[0] * h->A.fold[1] * h->A.fold[2];
+    for (int g = 0; g < 3; ++g) {
+        CK(h, cudaMemsetAsync(h->A.count[g], 0, B * sizeof(int), s));
+        CK(h, cudaMemsetAsync(h->A.bucket[g], 0, na * sizeof(int), s));
+    }
+    CK(h, cudaMemsetAsync(h->A.J, 0, na3 * sizeof(float), s));
+    CK(h, cudaMemsetAsync(h->A.U, 0, na3 * sizeof(float), s));
+    CK(h, cudaMemsetAsync(h->A.nnb, 0, na * sizeof(int), s));
+    CK(h, cudaMemsetAsync(h->A.D, 0, na3 * sizeof(float), s));
+    CK(h, cudaMemcpyAsync(h->A.order, h->ident, na * sizeof(int), cudaMemcpyDeviceToDevice, s));
+    CK(h, launch_md_prime(h->A, s));
+    CK(h, cudaMemcpyAsync(h->A.F, (ck ? h->ck_F : h->seg_F) + na3 * i, na3 * sizeof(float), cudaMemcpyDeviceToDevice, s));
+    h->steps = 0;
+    return LBMD_OK;
+}
+
+// One coupled step launched directly (not from the graph), recording the
+// substep positions, input velocities and forces, and keeping G and the
+// touched-node list for the reverse pass.
+lbmd_status enqueue_record_step(lbmd_t h) {
+    cudaStream_t s = h->stream;
+    AtomArgs A = h->A;
+    A.recP = h->recP;
+    A.recL = h->recL;
+    A.recV = h->recV;
+    A.recF = h->recF;
+    CouplingArgs C = h->C;
+    C.keep = 1;
+    CK(h, launch_md_sort(A, s));
+    CK(h, launch_interp(h->p.store, C, A, h->pop, s));
+    for (int k = 0; k <= A.n_md; ++k) CK(h, launch_md_substep(A, k, s));
+    CK(h, launch_spread(C, s));
+    CK(h, launch_lb_step(h->p.store, h->L, h->pop, h->ds, s));
+    CK(h, launch_lb_fix(h->p.store, h->L, h->pop, C, h->fix_grid, s));
+    ++h->steps;
+    return LBMD_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -397,6 +533,7 @@ lbmd_status lbmd_create(const lbmd_params *params, int n_atoms, const double *ma
             CREATE_TRY(dalloc_t(h, &A.sidx[g], (size_t)na));
         }
         CREATE_TRY(dalloc_t(h, &A.order, (size_t)na));
+        CREATE_TRY(dalloc_t(h, &h->ident, (size_t)na));
         CREATE_TRY(dalloc_t(h, &A.nbr, (size_t)na * NL_MAX));
         CREATE_TRY(dalloc_t(h, &A.nnb, (size_t)na));
         CREATE_TRY(dalloc_t(h, &A.D, na3));
@@ -456,6 +593,7 @@ void lbmd_destroy(lbmd_t h) {
     if (h->stream || h->s_main) cudaStreamSynchronize(h->stream);
     destroy_graph(h);
     for (void *p : h->allocs) cudaFree(p);
+    for (void *p : h->adj_allocs) cudaFree(p);
     if (h->stage) cudaFree(h->stage);
     if (h->ev_fork) cudaEventDestroy(h->ev_fork);
     if (h->ev_join) cudaEventDestroy(h->ev_join);
@@ -504,6 +642,7 @@ lbmd_status lbmd_set_state(lbmd_t h, const float *f, const float *rho, const flo
             std::vector<int> ident(h->na);
             for (int i = 0; i < h->na; ++i) ident[i] = i;
             CK(h, cudaMemcpy(h->A.order, ident.data(), h->na * sizeof(int), cudaMemcpyHostToDevice));
+            CK(h, cudaMemcpy(h->ident, ident.data(), h->na * sizeof(int), cudaMemcpyHostToDevice));
             CK(h, cudaMemsetAsync(h->A.nnb, 0, h->na * sizeof(int), h->stream));
             CK(h, cudaMemsetAsync(h->A.D, 0, na3 * sizeof(float), h->stream));
             const int one = 1;  // first force evaluation builds the lists
@@ -645,15 +784,98 @@ lbmd_status lbmd_set_timing_events(lbmd_t h, void *ev_start, void *ev_stop) {
 
 lbmd_status lbmd_backward(lbmd_t h, int n_steps, int ckpt_every, int observable, double *d_gamma, double *d_tau,
                           double *d_force_amp, double *obs) {
-    (void)n_steps;
-    (void)ckpt_every;
-    (void)observable;
-    (void)d_gamma;
-    (void)d_tau;
-    (void)d_force_amp;
-    (void)obs;
     if (!h) return fail(nullptr, LBMD_ERR_ARG, "handle is NULL");
-    return fail(h, LBMD_ERR_ARG, "lbmd_backward is not available in this build");
+    if (!h->state_set) return fail(h, LBMD_ERR_STATE, "lbmd_set_state has not been called");
+    if (n_steps < 1 || ckpt_every < 1) return fail(h, LBMD_ERR_ARG, "need n_steps >= 1 and ckpt_every >= 1");
+    if (observable != LBMD_OBS_DRAG_X && observable != LBMD_OBS_RG2) return fail(h, LBMD_ERR_ARG, "unknown observable");
+    if (h->na == 0) return fail(h, LBMD_ERR_ARG, "the observables need atoms (n_atoms > 0)");
+    TRY(adj_prepare(h, n_steps, ckpt_every));
+    cudaStream_t s = h->stream;
+    const int K = ckpt_every, nseg = (n_steps + K - 1) / K;
+    const int na = h->na;
+    if (!h->exec) TRY(build_graph(h));
+
+    // Forward pass with checkpoints, accumulating the observable.
+    CK(h, cudaMemsetAsync(h->obs_acc, 0, 8 * sizeof(double), s));
+    for (int n = 0; n < n_steps; ++n) {
+        if (n % K == 0) TRY(adj_save(h, n / K, true));
+        CK(h, cudaGraphLaunch(h->exec, s));
+        ++h->steps;
+        CK(h, launch_obs_accumulate(h->A, h->C, observable, h->obs_acc, s));
+    }
+    TRY(adj_save(h, nseg, true));  // final state, restored at the end
+    double acc = 0.0;
+    CK(h, cudaMemcpyAsync(&acc, h->obs_acc, sizeof(double), cudaMemcpyDeviceToHost, s));
+    CK(h, cudaStreamSynchronize(s));
+    TRY(read_flags(h));
+    const double O = acc / n_steps;
+
+    // Reverse pass, segment by segment.
+    AdjArgs &D = h->D;
+    D.L = h->L;
+    D.na = na;
+    D.obs_w = (float)(1.0 / n_steps);
+    D.observable = observable;
+    const size_t N = h->L.N, na3 = 3 * (size_t)na;
+    CK(h, cudaMemsetAsync(h->hat[0], 0, N * Q * sizeof(float), s));
+    CK(h, cudaMemsetAsync(D.Ghat, 0, N * sizeof(float4), s));
+    CK(h, cudaMemsetAsync(D.Uhat, 0, N * sizeof(float4), s));
+    CK(h, cudaMemsetAsync(D.xhat, 0, na3 * sizeof(float), s));
+    CK(h, cudaMemsetAsync(D.vhat, 0, na3 * sizeof(float), s));
+    CK(h, cudaMemsetAsync(D.gam_acc, 0, na * sizeof(double), s));
+    CK(h, cudaMemsetAsync(D.par_acc, 0, 2 * sizeof(double), s));
+    CK(h, cudaMemsetAsync(D.partials, 0, 2 * (size_t)h->adj_blocks * sizeof(double), s));
+    int cur = 0;
+    AtomArgs Aadj = h->A;
+    Aadj.count[0] = h->adj_count;
+    Aadj.slot[0] = h->adj_slot;
+    for (int seg = nseg - 1; seg >= 0; --seg) {
+        const int s0 = seg * K, s1 = std::min(s0 + K, n_steps);
+        TRY(adj_restore(h, seg, true));
+        for (int n = s0; n < s1; ++n) {
+            TRY(adj_save(h, n - s0, false));
+            CK(h, cudaGraphLaunch(h->exec, s));
+            ++h->steps;
+        }
+        for (int n = s1 - 1; n >= s0; --n) {
+            TRY(adj_restore(h, n - s0, false));
+            TRY(enqueue_record_step(h));  // step n again, keeping what the reverse needs
+            if (observable == LBMD_OBS_RG2) CK(h, launch_rg2_grad(h->A, h->obs_acc + 1, D.obs_w, D.xhat, s));
+            D.hat_in = h->hat[cur];
+            D.hat_out = h->hat[cur ^ 1];
+            AtomArgs Arec = h->A;
+            Arec.recP = h->recP;
+            Arec.recL = h->recL;
+            Arec.recV = h->recV;
+            Arec.recF = h->recF;
+            Aadj.recP = h->recP;
+            Aadj.recL = h->recL;
+            Aadj.recV = h->recV;
+            Aadj.recF = h->recF;
+            CK(h, launch_adjoint_step(h->p.store, D, Arec, Aadj, h->C, h->pop[0], s));
+            CK(h, cudaMemsetAsync(&h->ds->n_touched, 0, sizeof(int), s));
+            cur ^= 1;
+        }
+    }
+    // Parameter gradients: d/d gamma from the atoms, d/d omega and d/d A from
+    // the lattice (block partials plus touched-node corrections).
+    CK(h, launch_sum_double(D.gam_acc, na, h->obs_acc + 1, s));
+    CK(h, launch_sum_double(D.partials, h->adj_blocks, h->obs_acc + 2, s));
+    CK(h, launch_sum_double(D.partials + h->adj_blocks, h->adj_blocks, h->obs_acc + 3, s));
+    double res[3], corr[2];
+    CK(h, cudaMemcpyAsync(res, h->obs_acc + 1, 3 * sizeof(double), cudaMemcpyDeviceToHost, s));
+    CK(h, cudaMemcpyAsync(corr, D.par_acc, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
+    CK(h, cudaStreamSynchronize(s));
+    TRY(adj_restore(h, nseg, true));  // leave the state advanced by n_steps
+    CK(h, cudaStreamSynchronize(s));
+    TRY(read_flags(h));
+    const double om = 1.0 / h->p.tau;
+    const double omh = res[1] + corr[0];
+    if (obs) *obs = O;
+    if (d_gamma) *d_gamma = res[0];
+    if (d_tau) *d_tau = -omh * om * om;
+    if (d_force_amp) *d_force_amp = res[2] + corr[1];
+    return LBMD_OK;
 }
 
 }  // extern "C"

@@ -210,6 +210,8 @@ struct AtomArgs {
     int *count[3], *slot[3], *bucket[3], *sidx[3];  // pair-search buckets by generation mod 3
     int fmask[3];         // bucket coordinate = cell & fmask (fold = nc, or 64 with mask 63)
     int *order;           // atoms in warp-sorted (Morton bucket) order
+    float4 *recP, *recL;  // adjoint recording ((n_md+1)*na): positions at x_k, or NULL
+    float *recV, *recF;   // adjoint recording ((n_md+1)*3na): input velocity and force of kernel k
     int *nbr;             // na * NL_MAX neighbour lists (atom-major)
     int *nnb;             // list lengths
     float *D;             // 3*na drift since the last list build
@@ -232,6 +234,22 @@ struct CouplingArgs {
     int touched_cap;
     float4 *G;      // per node coupling force (x, y, z, unused)
     DevState *ds;
+    int keep;       // 1: the fix-up leaves G and the touched list for the adjoint
+};
+
+// Adjoint state and accumulators of lbmd_backward.
+struct AdjArgs {
+    Lat L;
+    int na;
+    float *hat_in, *hat_out;  // adjoint of the post-collision storage (19*N FP32): step n+1 in, n out
+    float4 *Ghat, *Uhat;      // per node hat F and hat u_b (touched nodes only, zero elsewhere)
+    float *xhat, *vhat;       // 3*na adjoint of positions and velocities
+    float *p, *Jhat, *Uat_hat, *xw;  // 3*na work arrays
+    double *gam_acc;          // na: d/d gamma contributions
+    double *par_acc;          // 2: touched-node corrections of d/d omega and d/d A
+    double *partials;         // 2*nblocks: block sums of d/d omega and d/d A
+    float obs_w;              // 1/T
+    int observable;
 };
 
 // Message returned by lbmd_last_error(NULL) on the calling thread.
@@ -255,6 +273,14 @@ cudaError_t launch_md_prime(const AtomArgs &a, cudaStream_t s);
 cudaError_t launch_md_substep(const AtomArgs &a, int k, cudaStream_t s);
 cudaError_t launch_md_diag(const AtomArgs &a, int *cell_of, int *neigh, cudaStream_t s);
 cudaError_t launch_md_sort(const AtomArgs &a, cudaStream_t s);
+
+int adj_lb_blocks(const Lat &L);
+cudaError_t launch_adjoint_step(int store, const AdjArgs &D, const AtomArgs &A, AtomArgs &Aadj, const CouplingArgs &C,
+                                const void *h, cudaStream_t s);
+cudaError_t launch_obs_accumulate(const AtomArgs &A, const CouplingArgs &C, int observable, double *out,
+                                  cudaStream_t s);
+cudaError_t launch_rg2_grad(const AtomArgs &A, double *scratch, float w, float *xhat, cudaStream_t s);
+cudaError_t launch_sum_double(const double *v, int n, double *out, cudaStream_t s);
 
 cudaError_t launch_interp(int store, const CouplingArgs &c, const AtomArgs &a, void *const buf[2], cudaStream_t s);
 cudaError_t launch_spread(const CouplingArgs &c, cudaStream_t s);

@@ -493,6 +493,13 @@ __global__ void __launch_bounds__(128) k_md_substep(AtomArgs A, int k) {
     const float im = A.inv_m[a];
     const float4 pa = A.P[par][a];
     const float4 la = A.L[par][a];
+    if (A.recP && valid) {
+        if (sub == 0) {
+            A.recP[(size_t)k * na + a] = pa;
+            A.recL[(size_t)k * na + a] = la;
+        }
+        if (sub < 3) A.recV[(size_t)k * 3 * na + sub * na + a] = vd;
+    }
     float F[3];
     if (k == 0) {
         F[0] = A.F[a];
@@ -515,6 +522,7 @@ __global__ void __launch_bounds__(128) k_md_substep(AtomArgs A, int k) {
     // Lanes 0-2: one velocity-Verlet component each.
     float v = vd, J = Jd, p = 0.f, lo = 0.f, Dd = 0.f;
     const float Fd = sub == 0 ? F[0] : (sub == 1 ? F[1] : F[2]);
+    if (A.recF && sub < 3) A.recF[(size_t)k * 3 * na + sub * na + a] = Fd;
     if (sub < 3) {
         if (k > 0) {  // second half-kick of substep k-1, drag at v_{k-1/2}
             const float drag = A.gamma * (Ud - v);

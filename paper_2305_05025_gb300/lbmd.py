@@ -279,3 +279,27 @@ def lbmd_destroy(h):
 
 def lbmd_version():
     return lib().lbmd_version()
+
+
+def observable_function():
+    """torch.autograd.Function over a differentiable rollout: forward runs
+    lbmd_backward (observable and its gradients in one pass, the state ends
+    advanced by n_steps), backward scales the stored gradients. Usage:
+    LBMDObservable.apply(gamma, tau, force_amp, handle, n_steps, ckpt_every,
+    observable) with 0-d float64 tensors for the three parameters."""
+    import torch
+
+    class LBMDObservable(torch.autograd.Function):
+        @staticmethod
+        def forward(ctx, gamma, tau, force_amp, handle, n_steps, ckpt_every, observable):
+            lbmd_set_physics(handle, float(gamma), float(tau), float(force_amp))
+            obs, dg, dt, da = lbmd_backward(handle, n_steps, ckpt_every, observable)
+            ctx.save_for_backward(torch.tensor([dg, dt, da], dtype=torch.float64))
+            return torch.tensor(obs, dtype=torch.float64)
+
+        @staticmethod
+        def backward(ctx, grad):
+            (d,) = ctx.saved_tensors
+            return grad * d[0], grad * d[1], grad * d[2], None, None, None, None
+
+    return LBMDObservable
