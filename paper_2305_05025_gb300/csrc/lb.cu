@@ -15,24 +15,139 @@ namespace lbmd {
 
 namespace {
 
+// Dense update of every node with F = g. Kept to few instructions per node
+// (the kernel issues about as fast as HBM delivers): the pull's neighbour
+// offsets are 32-bit per-thread constants (periodic wrap folded in), plane
+// i starts at i * plane_bytes, and the collision pairs each speed with its
+// opposite (collide_pairs).
 template <int S>
 __global__ void __launch_bounds__(256) k_lb_step(Lat L, typename Store<S>::T *b0, typename Store<S>::T *b1,
                                                  DevState *ds) {
+    using T = typename Store<S>::T;
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y * blockDim.y + threadIdx.y;
     const int z = blockIdx.z;
     if (x >= L.nx || y >= L.ny) return;
     const int step = ds->step;
-    const typename Store<S>::T *src = (step & 1) ? b1 : b0;
-    typename Store<S>::T *dst = (step & 1) ? b0 : b1;
-    float f[Q], g[3];
-    pull<S>(src, L, x, y, z, f);
-    body_force(L, x, y, z, g);
-    const float rho = collide(L, f, g);
-    if (!isfinite(rho)) atomicOr(&ds->flags, FLAG_NONFINITE);
-    const size_t node = ((size_t)z * L.ny + y) * L.nx + x;
+    const T *src = (step & 1) ? b1 : b0;
+    T *dst = (step & 1) ? b0 : b1;
+    const int nx = L.nx, nxy = L.nx * L.ny;
+    // Offset of the source node x - c for each sign of each component.
+    const int oxm = x == 0 ? nx - 1 : -1, oxp = x == nx - 1 ? 1 - nx : 1;
+    const int oym = y == 0 ? nxy - nx : -nx, oyp = y == L.ny - 1 ? nx - nxy : nx;
+    const int ozm = z == 0 ? (L.nz - 1) * nxy : -nxy, ozp = z == L.nz - 1 ? (1 - L.nz) * nxy : nxy;
+    const bool wlo = L.walls && z == 0, whi = L.walls && z == L.nz - 1;
+    const int node = z * nxy + y * nx + x;
+    const ptrdiff_t plane = (ptrdiff_t)L.N;
+    float f[Q];
+    const T *sp = src + node;  // node's entry in plane i, advanced plane by plane
 #pragma unroll
-    for (int i = 0; i < Q; ++i) Store<S>::st(dst + (size_t)i * L.N + node, f[i]);
+    for (int i = 0; i < Q; ++i) {
+        const int off = (cx(i) == 1 ? oxm : (cx(i) == -1 ? oxp : 0)) + (cy(i) == 1 ? oym : (cy(i) == -1 ? oyp : 0)) +
+                        (cz(i) == 1 ? ozm : (cz(i) == -1 ? ozp : 0));
+        const bool wall = (cz(i) == 1 && wlo) || (cz(i) == -1 && whi);
+        f[i] = Store<S>::ld(wall ? sp + (opp(i) - i) * plane : sp + off);
+        sp += plane;
+    }
+    float g[3];
+    body_force(L, x, y, z, g);
+    const float rho = collide_pairs(L, f, g);
+    if (!isfinite(rho)) atomicOr(&ds->flags, FLAG_NONFINITE);
+    T *dp = dst + node;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        Store<S>::st(dp, f[i]);
+        dp += plane;
+    }
+}
+
+// 16-bit helpers: a pair of neighbouring nodes' values as one 32-bit word
+// (node x0 in the low half, x0 + 1 in the high half).
+template <int S> struct Half16;
+template <> struct Half16<LBMD_F16_SHIFTED> {
+    static __device__ __forceinline__ float lo(unsigned w) { return __half2float(__ushort_as_half((unsigned short)(w & 0xffffu))); }
+    static __device__ __forceinline__ float hi(unsigned w) { return __half2float(__ushort_as_half((unsigned short)(w >> 16))); }
+    static __device__ __forceinline__ unsigned bits(float v) { return (unsigned)__half_as_ushort(__float2half_rn(v)); }
+};
+template <> struct Half16<LBMD_BF16_SHIFTED> {
+    static __device__ __forceinline__ float lo(unsigned w) { return __uint_as_float(w << 16); }
+    static __device__ __forceinline__ float hi(unsigned w) { return __uint_as_float(w & 0xffff0000u); }
+    static __device__ __forceinline__ unsigned bits(float v) {
+        return (unsigned)__bfloat16_as_ushort(__float2bfloat16_rn(v));
+    }
+};
+
+// 16-bit storage, nx even: each thread updates the node pair x0 = 2t, x0 + 1.
+// Every population of both nodes arrives as one aligned 32-bit load (kept
+// packed until used), the +-1 shift of the pull along x is assembled from the
+// neighbouring lane's word (or one 16-bit load at a row or warp edge), and
+// both results leave as one 32-bit store.
+template <int S>
+__global__ void __launch_bounds__(128, 7) k_lb_step_pair16(Lat L, typename Store<S>::T *b0, typename Store<S>::T *b1,
+                                                        DevState *ds) {
+    using T = typename Store<S>::T;
+    using H = Half16<S>;
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    const int z = blockIdx.z;
+    const int lane = (threadIdx.y * blockDim.x + threadIdx.x) & 31;
+    const int x0 = 2 * t;
+    const bool active = x0 < L.nx && y < L.ny;
+    const int xx = active ? x0 : 0, yy = active ? y : 0;
+    const int step = ds->step;
+    const T *src = (step & 1) ? b1 : b0;
+    T *dst = (step & 1) ? b0 : b1;
+    const int nx = L.nx, nxy = L.nx * L.ny;
+    const int oym = yy == 0 ? nxy - nx : -nx, oyp = yy == L.ny - 1 ? nx - nxy : nx;
+    const int ozm = z == 0 ? (L.nz - 1) * nxy : -nxy, ozp = z == L.nz - 1 ? (1 - L.nz) * nxy : nxy;
+    const bool wlo = L.walls && z == 0, whi = L.walls && z == L.nz - 1;
+    const int node = z * nxy + yy * nx + xx;
+    // A warp covers consecutive pairs of one row; lanes at its edges (or next
+    // to an inactive lane) load the shifted value themselves.
+    const int left_active = __shfl_up_sync(0xffffffffu, (int)active, 1);
+    const int right_active = __shfl_down_sync(0xffffffffu, (int)active, 1);
+    const bool left_ok = lane > 0 && xx > 0 && left_active;
+    const bool right_ok = lane < 31 && xx + 2 < nx && right_active;
+    const int xl = xx == 0 ? nx - 1 : -1;      // offset of x0 - 1
+    const int xr = xx + 2 == nx ? 2 - nx : 2;  // offset of x0 + 2
+    unsigned w[Q];
+    const ptrdiff_t plane = (ptrdiff_t)L.N;
+    const T *sp = src + node;  // the pair's entry in plane i, advanced plane by plane
+#pragma unroll
+    for (int i = 0; i < Q; ++i, sp += plane) {
+        const int oyz = (cy(i) == 1 ? oym : (cy(i) == -1 ? oyp : 0)) + (cz(i) == 1 ? ozm : (cz(i) == -1 ? ozp : 0));
+        const bool wall = (cz(i) == 1 && wlo) || (cz(i) == -1 && whi);
+        const T *row = wall ? sp + (opp(i) - i) * plane : sp + oyz;
+        const unsigned v = __ldg(reinterpret_cast<const unsigned *>(row));
+        if (cx(i) == 0) {
+            w[i] = v;
+        } else if (cx(i) == 1) {  // x0 pulls x0 - 1, x0 + 1 pulls x0
+            unsigned prev = __shfl_up_sync(0xffffffffu, v, 1) >> 16;
+            if (!left_ok) prev = (unsigned)__ldg(reinterpret_cast<const unsigned short *>(row + xl));
+            w[i] = wall ? v : (prev | (v << 16));
+        } else {  // x0 pulls x0 + 1, x0 + 1 pulls x0 + 2
+            unsigned next = __shfl_down_sync(0xffffffffu, v, 1) & 0xffffu;
+            if (!right_ok) next = (unsigned)__ldg(reinterpret_cast<const unsigned short *>(row + xr));
+            w[i] = wall ? v : ((v >> 16) | (next << 16));
+        }
+    }
+    if (!active) return;
+    float g[3], f[Q];
+    body_force(L, xx, yy, z, g);  // the pair kernel runs only when g is uniform along x
+#pragma unroll
+    for (int i = 0; i < Q; ++i) f[i] = H::lo(w[i]);
+    const float ra = collide_pairs(L, f, g);
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        const unsigned lo = H::bits(f[i]);
+        f[i] = H::hi(w[i]);
+        w[i] = lo;
+    }
+    const float rb = collide_pairs(L, f, g);
+    if (!isfinite(ra) || !isfinite(rb)) atomicOr(&ds->flags, FLAG_NONFINITE);
+    T *dp = dst + node;
+#pragma unroll
+    for (int i = 0; i < Q; ++i, dp += plane) __stcs(reinterpret_cast<unsigned *>(dp), w[i] | (H::bits(f[i]) << 16));
 }
 
 // Nodes touched by atoms: redo the collision with F = g + G from the same
@@ -256,6 +371,22 @@ dim3 node_grid(const Lat &L, dim3 b) { return dim3((L.nx + b.x - 1) / b.x, (L.ny
     }
 
 cudaError_t launch_lb_step(int store, const Lat &L, void *const buf[2], DevState *ds, cudaStream_t s) {
+    const bool pairs = store != LBMD_F32 && L.nx % 2 == 0 &&
+                       !(L.forcing == LBMD_FORCE_KOLMOGOROV && L.faxis == 0);
+    if (pairs) {
+        const int half = L.nx / 2;
+        int bx = ((half + 31) / 32) * 32;
+        if (bx > 128) bx = 128;
+        int by = 128 / bx;
+        if (by > L.ny) by = L.ny;
+        const dim3 b(bx, by, 1), g((half + bx - 1) / bx, (L.ny + by - 1) / by, L.nz);
+        if (store == LBMD_F16_SHIFTED)
+            k_lb_step_pair16<LBMD_F16_SHIFTED><<<g, b, 0, s>>>(L, (__half *)buf[0], (__half *)buf[1], ds);
+        else
+            k_lb_step_pair16<LBMD_BF16_SHIFTED>
+                <<<g, b, 0, s>>>(L, (__nv_bfloat16 *)buf[0], (__nv_bfloat16 *)buf[1], ds);
+        return cudaGetLastError();
+    }
     const dim3 b = node_block(L), g = node_grid(L, b);
     LBMD_DISPATCH(store, (k_lb_step<SV><<<g, b, 0, s>>>(L, (T *)buf[0], (T *)buf[1], ds)));
     return cudaGetLastError();

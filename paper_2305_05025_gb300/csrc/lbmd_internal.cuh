@@ -155,6 +155,49 @@ __device__ __forceinline__ float collide(const Lat &L, float f[Q], const float F
     return rho;
 }
 
+// Same collision as collide(), evaluated per pair of opposite speeds (i odd,
+// i + 1 = -c_i) with the per-node factors hoisted: with cu = c_i.u and
+// cF = c_i.F, the new value of speed i is
+//   (1 - omega) f_i + w_i (E + O),  of its opposite  (1 - omega) f_o + w_i (E - O),
+// E = A0 + cu (9/2 omega rho cu + 9 s cF),  O = 3 omega rho cu + 3 s cF,
+// A0 = omega (drho - 3/2 rho u.u) - 3 s u.F,  s = 1 - omega/2
+// (E is the even part of the equilibrium and Guo source, O the odd part).
+__device__ __forceinline__ float collide_pairs(const Lat &L, float f[Q], const float F[3]) {
+    float sp[9], dp[9];
+#pragma unroll
+    for (int p = 0; p < 9; ++p) {
+        sp[p] = f[2 * p + 1] + f[2 * p + 2];
+        dp[p] = f[2 * p + 1] - f[2 * p + 2];
+    }
+    float drho = f[0], jx = 0.f, jy = 0.f, jz = 0.f;
+#pragma unroll
+    for (int p = 0; p < 9; ++p) {
+        drho += sp[p];
+        if (cx(2 * p + 1)) jx += cx(2 * p + 1) * dp[p];
+        if (cy(2 * p + 1)) jy += cy(2 * p + 1) * dp[p];
+        if (cz(2 * p + 1)) jz += cz(2 * p + 1) * dp[p];
+    }
+    const float rho = L.rho0 + drho;
+    const float inv = 1.f / rho;
+    const float ux = (jx + 0.5f * F[0]) * inv, uy = (jy + 0.5f * F[1]) * inv, uz = (jz + 0.5f * F[2]) * inv;
+    const float usq = ux * ux + uy * uy + uz * uz;
+    const float uF = ux * F[0] + uy * F[1] + uz * F[2];
+    const float om = L.omega, s = 1.f - 0.5f * om, keep = 1.f - om;
+    const float A0 = om * (drho - 1.5f * rho * usq) - 3.f * s * uF;
+    const float k45 = 4.5f * om * rho, k3 = 3.f * om * rho, s9 = 9.f * s, s3 = 3.f * s;
+    f[0] = keep * f[0] + wgt(0) * A0;
+#pragma unroll
+    for (int i = 1; i < Q; i += 2) {
+        const float cu = cx(i) * ux + cy(i) * uy + cz(i) * uz;
+        const float cF = cx(i) * F[0] + cy(i) * F[1] + cz(i) * F[2];
+        const float E = A0 + cu * (k45 * cu + s9 * cF);
+        const float O = k3 * cu + s3 * cF;
+        f[i] = keep * f[i] + wgt(i) * (E + O);
+        f[i + 1] = keep * f[i + 1] + wgt(i) * (E - O);
+    }
+    return rho;
+}
+
 // Velocity u = (sum f c + g/2)/rho of a node from its pulled deviations.
 __device__ __forceinline__ float node_velocity(const Lat &L, const float f[Q], const float g[3], float u[3]) {
     float drho = 0.f, jx = 0.f, jy = 0.f, jz = 0.f;

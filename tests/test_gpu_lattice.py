@@ -27,18 +27,19 @@ def _cfg(**kw):
 
 @pytest.mark.parametrize("store", ["f32", "f16", "bf16"])
 @pytest.mark.parametrize("walls", [0, 1])
-def test_rest_state_is_bit_exact(store, walls):
-    cfg = _cfg(store=store, walls_z=walls, nx=17, ny=9, nz=6)
-    inp = lattice_inputs((17, 9, 6), 0.0, 1)
+@pytest.mark.parametrize("nx", [17, 66])  # odd: one node per thread; even: node pairs
+def test_rest_state_is_bit_exact(store, walls, nx):
+    cfg = _cfg(store=store, walls_z=walls, nx=nx, ny=9, nz=6)
+    inp = lattice_inputs((nx, 9, 6), 0.0, 1)
     h = make(cfg, inp)
     lbmd.lbmd_step(h, 25)
     out = lbmd.lbmd_get_fields(h, f=True, rho=True, u=True)
     w = np.array([1 / 3] + [1 / 18] * 6 + [1 / 36] * 12, np.float32)
-    assert np.array_equal(out["f"], np.repeat(w[:, None], 17 * 9 * 6, axis=1))
+    assert np.array_equal(out["f"], np.repeat(w[:, None], nx * 9 * 6, axis=1))
     assert np.all(out["rho"] == np.float32(1.0))
     assert np.all(out["u"] == 0.0)
     mass, pf, _ = lbmd.lbmd_get_stats(h)
-    assert mass == 17 * 9 * 6 and np.all(pf == 0.0)
+    assert mass == nx * 9 * 6 and np.all(pf == 0.0)
 
 
 def _free_run(orc, cfg, inp, steps):
@@ -65,6 +66,23 @@ def test_walls_poiseuille_matches_oracle(orc):
     cfg = _cfg(nx=8, ny=6, nz=20, tau=0.8, walls_z=1, forcing="poiseuille", force_amp=1e-5)
     inp = lattice_inputs((8, 6, 20), 0.005, 4)
     g, fo = _free_run(orc, cfg, inp, 100)
+    assert rel_linf(g["f"], fo) < TOL
+    assert rel_linf(g["u"], velocity(orc, cfg, fo)) < TOL
+
+
+@pytest.mark.parametrize("nx", [70, 96])  # pair kernel: row of 35 pairs (partial warp) and of 48 (warp edge)
+def test_pair_kernel_matches_oracle(orc, nx):
+    cfg = _cfg(nx=nx, ny=5, nz=4, tau=0.7, walls_z=1, forcing="kolmogorov", force_amp=1e-4, force_wave_axis=2)
+    inp = lattice_inputs((nx, 5, 4), 0.01, 8)
+    g, fo = _free_run(orc, cfg, inp, 40)
+    assert rel_linf(g["f"], fo) < TOL
+    assert rel_linf(g["u"], velocity(orc, cfg, fo)) < TOL
+
+
+def test_kolmogorov_along_x_matches_oracle(orc):
+    cfg = _cfg(nx=24, ny=6, nz=5, tau=0.9, forcing="kolmogorov", force_amp=1e-4, force_dir=1, force_wave_axis=0)
+    inp = lattice_inputs((24, 6, 5), 0.01, 9)
+    g, fo = _free_run(orc, cfg, inp, 40)
     assert rel_linf(g["f"], fo) < TOL
     assert rel_linf(g["u"], velocity(orc, cfg, fo)) < TOL
 
