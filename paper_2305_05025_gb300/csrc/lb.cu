@@ -65,9 +65,15 @@ __global__ void __launch_bounds__(256) k_lb_step(Lat L, typename Store<S>::T *b0
 // (node x0 in the low half, x0 + 1 in the high half).
 template <int S> struct Half16;
 template <> struct Half16<LBMD_F16_SHIFTED> {
-    static __device__ __forceinline__ float lo(unsigned w) { return __half2float(__ushort_as_half((unsigned short)(w & 0xffffu))); }
-    static __device__ __forceinline__ float hi(unsigned w) { return __half2float(__ushort_as_half((unsigned short)(w >> 16))); }
-    static __device__ __forceinline__ unsigned bits(float v) { return (unsigned)__half_as_ushort(__float2half_rn(v)); }
+    static __device__ __forceinline__ float lo(unsigned w) {
+        return __half2float(__ushort_as_half((unsigned short)(w & 0xffffu))) * kF16Unscale;
+    }
+    static __device__ __forceinline__ float hi(unsigned w) {
+        return __half2float(__ushort_as_half((unsigned short)(w >> 16))) * kF16Unscale;
+    }
+    static __device__ __forceinline__ unsigned bits(float v) {
+        return (unsigned)__half_as_ushort(__float2half_rn(v * kF16Scale));
+    }
 };
 template <> struct Half16<LBMD_BF16_SHIFTED> {
     static __device__ __forceinline__ float lo(unsigned w) { return __uint_as_float(w << 16); }

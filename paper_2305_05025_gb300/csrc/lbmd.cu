@@ -25,7 +25,7 @@ namespace {
 
 thread_local std::string g_create_error;
 
-constexpr int kFold = 64;  // bucket grid per axis (cells folded modulo this)
+constexpr int kFold = 128;  // bucket grid per axis (cells folded modulo this)
 constexpr int kCap = 64;   // atoms per bucket
 
 }  // namespace
@@ -537,8 +537,8 @@ lbmd_status lbmd_create(const lbmd_params *params, int n_atoms, const double *ma
         CREATE_TRY(dalloc_t(h, &A.nbr, (size_t)na * NL_MAX));
         CREATE_TRY(dalloc_t(h, &A.nnb, (size_t)na));
         CREATE_TRY(dalloc_t(h, &A.D, na3));
-        CREATE_TRY(dalloc_t(h, &A.scan_local, (size_t)64 * 64 * 64));
-        CREATE_TRY(dalloc_t(h, &A.scan_block, 256));
+        CREATE_TRY(dalloc_t(h, &A.scan_local, (size_t)kMortonCodes));
+        CREATE_TRY(dalloc_t(h, &A.scan_block, kMortonCodes / 1024));
         // Topology: masses and a symmetric bond CSR.
         std::vector<float> m(na), im(na);
         for (int a = 0; a < na; ++a) {

@@ -50,7 +50,8 @@ struct DevState {
     int nl_flag[3];  // neighbour-list rebuild requests, by generation mod 3
 };
 
-// Storage formats of the populations (delta f = f - w rho0 in every format).
+// Storage formats of the populations (delta f = f - w rho0 in every format;
+// FP16 scaled by 2^10).
 template <int S> struct Store;
 template <> struct Store<LBMD_F32> {
     using T = float;
@@ -59,12 +60,16 @@ template <> struct Store<LBMD_F32> {
     static __device__ __forceinline__ void st(T *p, float v) { __stcs(p, v); }
     static __device__ __forceinline__ void st_plain(T *p, float v) { *p = v; }
 };
+// FP16 holds 2^10 delta f: the exact power-of-two scale lifts the small
+// deviations of slow flows (down to ~1e-7) out of FP16's subnormal range,
+// and |delta f| up to 64 still fits.
+constexpr float kF16Scale = 1024.f, kF16Unscale = 1.f / 1024.f;
 template <> struct Store<LBMD_F16_SHIFTED> {
     using T = __half;
-    static __device__ __forceinline__ float ld(const T *p) { return __half2float(__ldg(p)); }
-    static __device__ __forceinline__ float ld_plain(const T *p) { return __half2float(*p); }
-    static __device__ __forceinline__ void st(T *p, float v) { __stcs(p, __float2half_rn(v)); }
-    static __device__ __forceinline__ void st_plain(T *p, float v) { *p = __float2half_rn(v); }
+    static __device__ __forceinline__ float ld(const T *p) { return __half2float(__ldg(p)) * kF16Unscale; }
+    static __device__ __forceinline__ float ld_plain(const T *p) { return __half2float(*p) * kF16Unscale; }
+    static __device__ __forceinline__ void st(T *p, float v) { __stcs(p, __float2half_rn(v * kF16Scale)); }
+    static __device__ __forceinline__ void st_plain(T *p, float v) { *p = __float2half_rn(v * kF16Scale); }
 };
 template <> struct Store<LBMD_BF16_SHIFTED> {
     using T = __nv_bfloat16;
@@ -227,6 +232,8 @@ __device__ __forceinline__ float node_velocity(const Lat &L, const float f[Q], c
 // relative error before its final rounding.
 
 constexpr int CREF_BITS = 10;  // cref packs three cell coordinates < 1024
+constexpr int kMortonBits = 7;                              // bucket coordinates < 128
+constexpr int kMortonCodes = 1 << (3 * kMortonBits);       // 2^21 Morton codes
 constexpr int NL_MAX = 256;    // neighbour-list capacity per atom (close packing of sigma = 0.4 beads within 1.3: ~200)
 
 struct AtomArgs {
@@ -251,7 +258,7 @@ struct AtomArgs {
     const int *bstart, *bpart;  // bond CSR
     const float *bk, *br0;
     int *count[3], *slot[3], *bucket[3], *sidx[3];  // pair-search buckets by generation mod 3
-    int fmask[3];         // bucket coordinate = cell & fmask (fold = nc, or 64 with mask 63)
+    int fmask[3];         // bucket coordinate = cell & fmask (fold = nc, or 128 with mask 127)
     int *order;           // atoms in warp-sorted (Morton bucket) order
     float4 *recP, *recL;  // adjoint recording ((n_md+1)*na): positions at x_k, or NULL
     float *recV, *recF;   // adjoint recording ((n_md+1)*3na): input velocity and force of kernel k
@@ -260,8 +267,8 @@ struct AtomArgs {
     float *D;             // 3*na drift since the last list build
     float rl2;            // (rc + skin)^2, list radius squared
     float half_skin2;     // (skin/2)^2, drift that triggers a rebuild
-    int *scan_local;      // 64^3 Morton-code exclusive scan within blocks of 1024
-    int *scan_block;      // 256 block offsets
+    int *scan_local;      // Morton-code exclusive scan within blocks of 1024
+    int *scan_block;      // kMortonCodes / 1024 block offsets
     DevState *ds;
 };
 

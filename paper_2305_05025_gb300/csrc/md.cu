@@ -99,8 +99,8 @@ __device__ __forceinline__ float bond_factor(const float dh[3], const float dl[3
     return -k * (diff / (r + r0)) / r;
 }
 
-// Bucket of a cell: cells fold onto a grid of at most 64 per axis (fold = nc
-// when nc <= 64, otherwise 64 and fmask = 63).
+// Bucket of a cell: cells fold onto a grid of at most 128 per axis (fold = nc
+// when nc <= 128, otherwise 128 and fmask = 127).
 __device__ __forceinline__ int bucket_of(const AtomArgs &A, const int c[3]) {
     return ((c[2] & A.fmask[2]) * A.fold[1] + (c[1] & A.fmask[1])) * A.fold[0] + (c[0] & A.fmask[0]);
 }
@@ -216,12 +216,12 @@ __device__ __forceinline__ void insert(const AtomArgs &A, int g3, int a, const i
 
 // ---------------------------------------------------------------------------
 // Warp-sorted order: counting sort of the atoms by bucket, buckets taken in
-// Morton order over a 64^3 grid (codes outside the bucket grid count zero).
+// Morton order over a 128^3 grid (codes outside the bucket grid count zero).
 
 __device__ __forceinline__ unsigned spread3(unsigned v) {
     unsigned r = 0;
 #pragma unroll
-    for (int i = 0; i < 6; ++i) r |= ((v >> i) & 1u) << (3 * i);
+    for (int i = 0; i < kMortonBits; ++i) r |= ((v >> i) & 1u) << (3 * i);
     return r;
 }
 
@@ -232,7 +232,7 @@ __device__ __forceinline__ unsigned morton3(int x, int y, int z) {
 __device__ __forceinline__ int compact3(unsigned m) {
     int r = 0;
 #pragma unroll
-    for (int i = 0; i < 6; ++i) r |= (int)((m >> (3 * i)) & 1u) << i;
+    for (int i = 0; i < kMortonBits; ++i) r |= (int)((m >> (3 * i)) & 1u) << i;
     return r;
 }
 
@@ -269,19 +269,25 @@ __global__ void __launch_bounds__(1024) k_sort_local(AtomArgs A) {
     if (threadIdx.x == 1023) A.scan_block[blockIdx.x] = before + incl;
 }
 
-// Exclusive scan of the 256 block totals.
-__global__ void __launch_bounds__(256) k_sort_top(AtomArgs A) {
-    __shared__ int sh[256];
+// Exclusive scan of the kMortonCodes/1024 block totals (one block, two
+// totals per thread).
+__global__ void __launch_bounds__(1024) k_sort_top(AtomArgs A) {
+    constexpr int NB = kMortonCodes / 1024;
+    __shared__ int sh[1024];
     const int t = threadIdx.x;
-    sh[t] = A.scan_block[t];
+    const int a0 = A.scan_block[2 * t], a1 = A.scan_block[2 * t + 1];
+    sh[t] = a0 + a1;
     __syncthreads();
-    for (int o = 1; o < 256; o <<= 1) {
+    for (int o = 1; o < 1024; o <<= 1) {
         const int v = t >= o ? sh[t - o] : 0;
         __syncthreads();
         sh[t] += v;
         __syncthreads();
     }
-    A.scan_block[t] = t ? sh[t - 1] : 0;
+    const int before = t ? sh[t - 1] : 0;
+    static_assert(NB == 2048, "two block totals per thread");
+    A.scan_block[2 * t] = before;
+    A.scan_block[2 * t + 1] = before + a0;
 }
 
 __global__ void __launch_bounds__(128) k_sort_scatter(AtomArgs A) {
@@ -659,8 +665,8 @@ cudaError_t launch_md_substep(const AtomArgs &a, int k, cudaStream_t s) {
 
 cudaError_t launch_md_sort(const AtomArgs &a, cudaStream_t s) {
     if (a.na == 0) return cudaSuccess;
-    k_sort_local<<<256, 1024, 0, s>>>(a);
-    k_sort_top<<<1, 256, 0, s>>>(a);
+    k_sort_local<<<kMortonCodes / 1024, 1024, 0, s>>>(a);
+    k_sort_top<<<1, 1024, 0, s>>>(a);
     k_sort_scatter<<<(a.na + 127) / 128, 128, 0, s>>>(a);
     return cudaGetLastError();
 }

@@ -73,7 +73,7 @@ def test_single_atom_in_uniform_flow(n_md):
     # FP64 sums of FP32 populations: the fluid momentum carries ~1e-7 of its
     # own magnitude in rounding.
     assert abs((pf1[0] - pf0[0]) + J) < 1e-6 * J + 2e-7 * abs(pf0[0])
-    assert abs(m1 - m0) < 1e-9
+    assert abs(m1 - m0) < 1e-8  # FP32 rounding of 64 nodes' populations
 
 
 def _teacher_forced(orc, cfg, inp, steps):
