@@ -199,6 +199,54 @@ def cpu_baseline(cfg, inp, steps=3):
                       f"{dt:.1f} s"}
 
 
+ADJOINT_WORKLOAD = "chain5k_lattice64_uniform"
+
+
+def adjoint_timing(stream):
+    """Forward + discrete adjoint of the 64^3 / 5,000-bead workload: 200
+    steps, checkpoints every 20, gradient of the mean drag with respect to
+    gamma, tau and the forcing amplitude; timed with CUDA events around one
+    lbmd_backward call, after one untimed call."""
+    import torch
+
+    from paper_2305_05025_gb300 import lbmd
+
+    cfg = synth.workload(ADJOINT_WORKLOAD, **DEFAULT_OVERRIDES)
+    inp = synth.inputs(cfg, 1)
+    steps, ckpt = cfg["steps"], cfg["ckpt_every"]
+
+    def fresh():
+        h = lbmd.lbmd_create(cfg, inp["mass"], inp["bonds"], inp["bond_k"], inp["bond_r0"])
+        lbmd.lbmd_set_state(h, rho=inp["rho"].astype(np.float32), u=inp["u"].astype(np.float32), x=inp["x"],
+                            v=inp["v"].astype(np.float32))
+        return h
+
+    h = fresh()
+    lbmd.lbmd_backward(h, steps, ckpt, lbmd.OBS_DRAG_X)
+    lbmd.lbmd_destroy(h)
+    h = fresh()
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    t0.record(stream)
+    lbmd.lbmd_backward(h, steps, ckpt, lbmd.OBS_DRAG_X)
+    t1.record(stream)
+    torch.cuda.synchronize()
+    ms = t0.elapsed_time(t1)
+    lbmd.lbmd_destroy(h)
+    h = fresh()
+    torch.cuda.synchronize()
+    t0.record(stream)
+    lbmd.lbmd_step(h, steps)
+    t1.record(stream)
+    torch.cuda.synchronize()
+    ms_fwd = t0.elapsed_time(t1)
+    lbmd.lbmd_destroy(h)
+    nodes = cfg["nx"] * cfg["ny"] * cfg["nz"]
+    return {"workload": ADJOINT_WORKLOAD, "steps": steps, "ckpt_every": ckpt, "n_md": cfg["n_md"],
+            "gamma": cfg["gamma"], "ms_forward_and_adjoint": ms, "ms_forward_only": ms_fwd,
+            "adjoint_over_forward": ms / ms_fwd, "mlups_forward_and_adjoint": nodes * steps / (ms * 1e-3) / 1e6}
+
+
 def run_ours(args, cfg):
     import torch
 
@@ -293,6 +341,8 @@ def run_ours(args, cfg):
            "clocks": clk.result}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(cfg, inp)
+    if world == 1 and not args.no_adjoint:
+        out["adjoint"] = adjoint_timing(stream)
     if world > 1:
         import torch.distributed as dist
 
@@ -310,6 +360,7 @@ def main():
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD)
     ap.add_argument("--store", default="f32", choices=["f32", "f16", "bf16"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-adjoint", action="store_true", help="skip the timing of the adjoint workload")
     args = ap.parse_args()
     overrides = dict(DEFAULT_OVERRIDES)
     overrides["store"] = args.store

@@ -250,54 +250,92 @@ __device__ __forceinline__ void hvp_add(float phi, float dphi_r, const float d[3
 }
 
 // K4: hat x_a += sum_b K_ab(x_k) (p_a - p_b), LJ pairs within rc (27 cells of
-// the adjoint buckets) and bonds; one thread per atom.
-__global__ void k_adj_hvp(AdjArgs D, AtomArgs A, int k) {
-    const int a = blockIdx.x * blockDim.x + threadIdx.x;
-    if (a >= D.na) return;
+// the adjoint buckets) and bonds. One warp per atom: the candidates of the
+// neighbour cells within reach of rc are numbered by a warp prefix sum over
+// the cell counts and dealt to the lanes; bonded partners (the first 32) sit
+// one per lane and are matched with shuffles; the lanes' terms are summed
+// across the warp.
+__global__ void __launch_bounds__(128) k_adj_hvp(AdjArgs D, AtomArgs A, int k) {
+    const int lane = threadIdx.x & 31;
+    const int a = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (a >= D.na) return;  // whole warp
     const int na = D.na;
     const float4 *P = A.recP + (size_t)k * na, *Lr = A.recL + (size_t)k * na;
     const float4 pa = P[a], la = Lr[a];
     const float pA[3] = {D.p[a], D.p[na + a], D.p[2 * na + a]};
-    int cr[3], cc[3];
+    const int b0 = A.bstart[a], b1 = A.bstart[a + 1];
+    const int nbond = b1 - b0;
+    const int partner = lane < nbond ? A.bpart[b0 + lane] : -1;
     const unsigned ua = __float_as_uint(pa.w);
     const float pp[3] = {pa.x, pa.y, pa.z};
+    int cc[3];
+    float t[3];  // position within the current cell
     for (int d = 0; d < 3; ++d) {
-        cr[d] = (int)((ua >> (CREF_BITS * d)) & 1023u);
-        int c = (cr[d] + (int)floorf(pp[d] * A.inv_h[d])) % A.nc[d];
+        const int cr = (int)((ua >> (CREF_BITS * d)) & 1023u);
+        const float fl = floorf(pp[d] * A.inv_h[d]);
+        t[d] = pp[d] - fl * A.h[d];
+        int c = (cr + (int)fl) % A.nc[d];
         cc[d] = c < 0 ? c + A.nc[d] : c;
     }
+    int bucket = 0, n = 0;
+    if (lane < 27) {
+        const int o[3] = {lane % 3 - 1, (lane / 3) % 3 - 1, lane / 9 - 1};
+        float gap2 = 0.f;  // squared distance to the neighbour cell (conservative margin below)
+        for (int d = 0; d < 3; ++d) {
+            const float g = o[d] < 0 ? t[d] : (o[d] > 0 ? A.h[d] - t[d] : 0.f);
+            gap2 += g * g;
+        }
+        if (gap2 < A.rc2f * 1.0001f) {
+            int c[3];
+            for (int d = 0; d < 3; ++d) {
+                const int v = (cc[d] + o[d]) % A.nc[d];
+                c[d] = v < 0 ? v + A.nc[d] : v;
+            }
+            bucket = ((c[2] & A.fmask[2]) * A.fold[1] + (c[1] & A.fmask[1])) * A.fold[0] + (c[0] & A.fmask[0]);
+            n = min(A.count[0][bucket], A.cap);
+        }
+    }
+    int incl = n;
+    for (int o = 1; o < 32; o <<= 1) {
+        const int v = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += v;
+    }
+    const int total = __shfl_sync(0xffffffffu, incl, 31);
     float out[3] = {0.f, 0.f, 0.f};
     const float s6 = A.lj_sig2 * A.lj_sig2 * A.lj_sig2;
-    for (int oz = -1; oz <= 1; ++oz)
-        for (int oy = -1; oy <= 1; ++oy)
-            for (int ox = -1; ox <= 1; ++ox) {
-                const int o[3] = {ox, oy, oz};
-                int c[3];
-                for (int d = 0; d < 3; ++d) {
-                    int v = (cc[d] + o[d]) % A.nc[d];
-                    c[d] = v < 0 ? v + A.nc[d] : v;
-                }
-                const int b = ((c[2] & A.fmask[2]) * A.fold[1] + (c[1] & A.fmask[1])) * A.fold[0] + (c[0] & A.fmask[0]);
-                const int n = min(A.count[0][b], A.cap);
-                for (int j = 0; j < n; ++j) {
-                    const int q = A.slot[0][(size_t)b * A.cap + j];
-                    if (q == a) continue;
-                    float d[3];
-                    rec_disp(A, pa, la, P[q], Lr[q], d);
-                    const float r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
-                    if (!(r2 < A.rc2f) || is_bonded(A, a, q)) continue;
-                    const float r = sqrtf(r2);
-                    const float ir2 = 1.f / r2;
-                    const float ir6 = ir2 * ir2 * ir2, ir8 = ir6 * ir2;
-                    // phi = 24 eps s6 (2 s6 r^-14 - r^-8) - fc / r
-                    const float phi = A.lj_24eps * s6 * ir8 * (2.f * s6 * ir6 - 1.f) - A.lj_fc / r;
-                    // phi'/r = 24 eps s6 (-28 s6 r^-16 + 8 r^-10) + fc r^-3
-                    const float dphi_r = A.lj_24eps * s6 * ir8 * ir2 * (-28.f * s6 * ir6 + 8.f) + A.lj_fc * ir2 / r;
-                    const float dp[3] = {pA[0] - D.p[q], pA[1] - D.p[na + q], pA[2] - D.p[2 * na + q]};
-                    hvp_add(phi, dphi_r, d, dp, out);
-                }
-            }
-    for (int s = A.bstart[a]; s < A.bstart[a + 1]; ++s) {
+    for (int t0 = lane; t0 - lane < total; t0 += 32) {
+        int pos = 0;  // cell holding candidate t0: first lane whose inclusive sum exceeds it
+        for (int step = 16; step > 0; step >>= 1) {
+            const int probe = __shfl_sync(0xffffffffu, incl, pos + step - 1);
+            if (probe <= t0) pos += step;
+        }
+        const int cb = __shfl_sync(0xffffffffu, bucket, pos & 31);
+        const int before = __shfl_sync(0xffffffffu, incl - n, pos & 31);
+        const int q = t0 < total ? A.slot[0][(size_t)cb * A.cap + (t0 - before)] : a;
+        bool use = false;
+        float d[3] = {0.f, 0.f, 0.f};
+        float r2 = 1.f;
+        if (q != a) {
+            rec_disp(A, pa, la, P[q], Lr[q], d);
+            r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+            use = r2 < A.rc2f;
+        }
+        bool bonded_q = false;
+        for (int l = 0; l < min(nbond, 32); ++l) bonded_q |= __shfl_sync(0xffffffffu, partner, l) == q;
+        if (use && nbond > 32 && !bonded_q) bonded_q = is_bonded(A, a, q);
+        if (use && !bonded_q) {
+            const float r = sqrtf(r2);
+            const float ir2 = 1.f / r2;
+            const float ir6 = ir2 * ir2 * ir2, ir8 = ir6 * ir2;
+            // phi = 24 eps s6 (2 s6 r^-14 - r^-8) - fc / r
+            const float phi = A.lj_24eps * s6 * ir8 * (2.f * s6 * ir6 - 1.f) - A.lj_fc / r;
+            // phi'/r = 24 eps s6 (-28 s6 r^-16 + 8 r^-10) + fc r^-3
+            const float dphi_r = A.lj_24eps * s6 * ir8 * ir2 * (-28.f * s6 * ir6 + 8.f) + A.lj_fc * ir2 / r;
+            const float dp[3] = {pA[0] - D.p[q], pA[1] - D.p[na + q], pA[2] - D.p[2 * na + q]};
+            hvp_add(phi, dphi_r, d, dp, out);
+        }
+    }
+    for (int s = b0 + lane; s < b1; s += 32) {
         const int q = A.bpart[s];
         float d[3];
         rec_disp(A, pa, la, P[q], Lr[q], d);
@@ -308,7 +346,10 @@ __global__ void k_adj_hvp(AdjArgs D, AtomArgs A, int k) {
         const float dp[3] = {pA[0] - D.p[q], pA[1] - D.p[na + q], pA[2] - D.p[2 * na + q]};
         hvp_add(phi, dphi_r, d, dp, out);
     }
-    for (int d = 0; d < 3; ++d) D.xhat[d * na + a] += out[d];
+    for (int o = 16; o > 0; o >>= 1)
+        for (int d = 0; d < 3; ++d) out[d] += __shfl_xor_sync(0xffffffffu, out[d], o);
+    if (lane == 0)
+        for (int d = 0; d < 3; ++d) D.xhat[d * na + a] += out[d];
 }
 
 // K5: interpolation adjoint. U_a = sum_j W_aj u_b(j): hat u_b(j) += W_aj hat U_a
@@ -563,7 +604,7 @@ cudaError_t launch_adjoint_step(int store, const AdjArgs &D, const AtomArgs &A, 
             cudaError_t e = cudaMemsetAsync(Aadj.count[0], 0, B * sizeof(int), s);
             if (e != cudaSuccess) return e;
             k_adj_bins<<<ga, 128, 0, s>>>(Aadj, k);
-            k_adj_hvp<<<ga, 128, 0, s>>>(D, Aadj, k);
+            k_adj_hvp<<<(na + 3) / 4, 128, 0, s>>>(D, Aadj, k);  // a warp per atom
         }
         ADJ_DISPATCH(store, (k_adj_interp<SV><<<ga, 128, 0, s>>>(D, C, (const T *)h)));
     }

@@ -15,12 +15,29 @@ namespace lbmd {
 
 namespace {
 
+// The 19 pulled values of one node from its entry sp in plane 0; W: this z
+// plane borders a wall (half-way bounce-back from the node's own opposite
+// population).
+template <int S, bool W>
+__device__ __forceinline__ void pull_node(const typename Store<S>::T *sp, ptrdiff_t plane, int oxm, int oxp, int oym,
+                                          int oyp, int ozm, int ozp, bool wlo, bool whi, float f[Q]) {
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        const int off = (cx(i) == 1 ? oxm : (cx(i) == -1 ? oxp : 0)) + (cy(i) == 1 ? oym : (cy(i) == -1 ? oyp : 0)) +
+                        (cz(i) == 1 ? ozm : (cz(i) == -1 ? ozp : 0));
+        const bool wall = W && ((cz(i) == 1 && wlo) || (cz(i) == -1 && whi));
+        f[i] = Store<S>::ld_raw(wall ? sp + (opp(i) - i) * plane : sp + off);
+        sp += plane;
+    }
+}
+
 // Dense update of every node with F = g. Kept to few instructions per node
 // (the kernel issues about as fast as HBM delivers): the pull's neighbour
 // offsets are 32-bit per-thread constants (periodic wrap folded in), plane
 // i starts at i * plane_bytes, and the collision pairs each speed with its
-// opposite (collide_pairs).
-template <int S>
+// opposite and is specialised on the direction FD of the body force
+// (collide_g), in stored units.
+template <int S, int FD>
 __global__ void __launch_bounds__(256) k_lb_step(Lat L, typename Store<S>::T *b0, typename Store<S>::T *b1,
                                                  DevState *ds) {
     using T = typename Store<S>::T;
@@ -40,23 +57,18 @@ __global__ void __launch_bounds__(256) k_lb_step(Lat L, typename Store<S>::T *b0
     const int node = z * nxy + y * nx + x;
     const ptrdiff_t plane = (ptrdiff_t)L.N;
     float f[Q];
-    const T *sp = src + node;  // node's entry in plane i, advanced plane by plane
-#pragma unroll
-    for (int i = 0; i < Q; ++i) {
-        const int off = (cx(i) == 1 ? oxm : (cx(i) == -1 ? oxp : 0)) + (cy(i) == 1 ? oym : (cy(i) == -1 ? oyp : 0)) +
-                        (cz(i) == 1 ? ozm : (cz(i) == -1 ? ozp : 0));
-        const bool wall = (cz(i) == 1 && wlo) || (cz(i) == -1 && whi);
-        f[i] = Store<S>::ld(wall ? sp + (opp(i) - i) * plane : sp + off);
-        sp += plane;
-    }
-    float g[3];
-    body_force(L, x, y, z, g);
-    const float rho = collide_pairs(L, f, g);
+    // Only the first and last planes of a walled lattice test for walls (the
+    // branch is uniform: a block holds one z plane).
+    if (wlo || whi)
+        pull_node<S, true>(src + node, plane, oxm, oxp, oym, oyp, ozm, ozp, wlo, whi, f);
+    else
+        pull_node<S, false>(src + node, plane, oxm, oxp, oym, oyp, ozm, ozp, false, false, f);
+    const float rho = collide_g<FD, Store<S>::kScaled>(L, f, body_amp(L, x, y, z));
     if (!isfinite(rho)) atomicOr(&ds->flags, FLAG_NONFINITE);
     T *dp = dst + node;
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
-        Store<S>::st(dp, f[i]);
+        Store<S>::st_raw(dp, f[i]);
         dp += plane;
     }
 }
@@ -65,30 +77,66 @@ __global__ void __launch_bounds__(256) k_lb_step(Lat L, typename Store<S>::T *b0
 // (node x0 in the low half, x0 + 1 in the high half).
 template <int S> struct Half16;
 template <> struct Half16<LBMD_F16_SHIFTED> {
-    static __device__ __forceinline__ float lo(unsigned w) {
-        return __half2float(__ushort_as_half((unsigned short)(w & 0xffffu))) * kF16Unscale;
+    // (low, high) halves of a word as floats, in stored units.
+    static __device__ __forceinline__ float2 unpack(unsigned w) {
+        __half2 h;
+        memcpy(&h, &w, 4);
+        return __half22float2(h);
     }
-    static __device__ __forceinline__ float hi(unsigned w) {
-        return __half2float(__ushort_as_half((unsigned short)(w >> 16))) * kF16Unscale;
-    }
-    static __device__ __forceinline__ unsigned bits(float v) {
-        return (unsigned)__half_as_ushort(__float2half_rn(v * kF16Scale));
+    static __device__ __forceinline__ unsigned pack(float lo, float hi) {
+        const __half2 h = __floats2half2_rn(lo, hi);
+        unsigned w;
+        memcpy(&w, &h, 4);
+        return w;
     }
 };
 template <> struct Half16<LBMD_BF16_SHIFTED> {
-    static __device__ __forceinline__ float lo(unsigned w) { return __uint_as_float(w << 16); }
-    static __device__ __forceinline__ float hi(unsigned w) { return __uint_as_float(w & 0xffff0000u); }
-    static __device__ __forceinline__ unsigned bits(float v) {
-        return (unsigned)__bfloat16_as_ushort(__float2bfloat16_rn(v));
+    static __device__ __forceinline__ float2 unpack(unsigned w) {
+        return make_float2(__uint_as_float(w << 16), __uint_as_float(w & 0xffff0000u));
+    }
+    static __device__ __forceinline__ unsigned pack(float lo, float hi) {
+        const __nv_bfloat162 h = __floats2bfloat162_rn(lo, hi);
+        unsigned w;
+        memcpy(&w, &h, 4);
+        return w;
     }
 };
+
+// The 19 pulled words (two nodes each) of a node pair from its entry sp in
+// plane 0. The +-1 shift along x comes from the neighbouring lane's word
+// (byte permutes), or from one 16-bit load at a row or warp edge; W: this z
+// plane borders a wall.
+template <int S, bool W>
+__device__ __forceinline__ void pull_pair(const typename Store<S>::T *sp, ptrdiff_t plane, int oym, int oyp, int ozm,
+                                          int ozp, bool wlo, bool whi, bool left_ok, bool right_ok, int xl, int xr,
+                                          unsigned w[Q]) {
+    using T = typename Store<S>::T;
+#pragma unroll
+    for (int i = 0; i < Q; ++i, sp += plane) {
+        const int oyz = (cy(i) == 1 ? oym : (cy(i) == -1 ? oyp : 0)) + (cz(i) == 1 ? ozm : (cz(i) == -1 ? ozp : 0));
+        const bool wall = W && ((cz(i) == 1 && wlo) || (cz(i) == -1 && whi));
+        const T *row = wall ? sp + (opp(i) - i) * plane : sp + oyz;
+        const unsigned v = __ldg(reinterpret_cast<const unsigned *>(row));
+        if (cx(i) == 0) {
+            w[i] = v;
+        } else if (cx(i) == 1) {  // x0 pulls x0 - 1 (high half of the left word), x0 + 1 pulls x0
+            unsigned prev = __shfl_up_sync(0xffffffffu, v, 1);
+            if (!left_ok) prev = (unsigned)__ldg(reinterpret_cast<const unsigned short *>(row + xl)) << 16;
+            w[i] = wall ? v : __byte_perm(prev, v, 0x5432);
+        } else {  // x0 pulls x0 + 1, x0 + 1 pulls x0 + 2 (low half of the right word)
+            unsigned next = __shfl_down_sync(0xffffffffu, v, 1);
+            if (!right_ok) next = (unsigned)__ldg(reinterpret_cast<const unsigned short *>(row + xr));
+            w[i] = wall ? v : __byte_perm(v, next, 0x5432);
+        }
+    }
+}
 
 // 16-bit storage, nx even: each thread updates the node pair x0 = 2t, x0 + 1.
 // Every population of both nodes arrives as one aligned 32-bit load (kept
 // packed until used), the +-1 shift of the pull along x is assembled from the
 // neighbouring lane's word (or one 16-bit load at a row or warp edge), and
 // both results leave as one 32-bit store.
-template <int S>
+template <int S, int FD>
 __global__ void __launch_bounds__(128, 7) k_lb_step_pair16(Lat L, typename Store<S>::T *b0, typename Store<S>::T *b1,
                                                         DevState *ds) {
     using T = typename Store<S>::T;
@@ -118,42 +166,27 @@ __global__ void __launch_bounds__(128, 7) k_lb_step_pair16(Lat L, typename Store
     const int xr = xx + 2 == nx ? 2 - nx : 2;  // offset of x0 + 2
     unsigned w[Q];
     const ptrdiff_t plane = (ptrdiff_t)L.N;
-    const T *sp = src + node;  // the pair's entry in plane i, advanced plane by plane
-#pragma unroll
-    for (int i = 0; i < Q; ++i, sp += plane) {
-        const int oyz = (cy(i) == 1 ? oym : (cy(i) == -1 ? oyp : 0)) + (cz(i) == 1 ? ozm : (cz(i) == -1 ? ozp : 0));
-        const bool wall = (cz(i) == 1 && wlo) || (cz(i) == -1 && whi);
-        const T *row = wall ? sp + (opp(i) - i) * plane : sp + oyz;
-        const unsigned v = __ldg(reinterpret_cast<const unsigned *>(row));
-        if (cx(i) == 0) {
-            w[i] = v;
-        } else if (cx(i) == 1) {  // x0 pulls x0 - 1, x0 + 1 pulls x0
-            unsigned prev = __shfl_up_sync(0xffffffffu, v, 1) >> 16;
-            if (!left_ok) prev = (unsigned)__ldg(reinterpret_cast<const unsigned short *>(row + xl));
-            w[i] = wall ? v : (prev | (v << 16));
-        } else {  // x0 pulls x0 + 1, x0 + 1 pulls x0 + 2
-            unsigned next = __shfl_down_sync(0xffffffffu, v, 1) & 0xffffu;
-            if (!right_ok) next = (unsigned)__ldg(reinterpret_cast<const unsigned short *>(row + xr));
-            w[i] = wall ? v : ((v >> 16) | (next << 16));
-        }
-    }
+    // Uniform branch: a block holds one z plane.
+    if (wlo || whi)
+        pull_pair<S, true>(src + node, plane, oym, oyp, ozm, ozp, wlo, whi, left_ok, right_ok, xl, xr, w);
+    else
+        pull_pair<S, false>(src + node, plane, oym, oyp, ozm, ozp, false, false, left_ok, right_ok, xl, xr, w);
     if (!active) return;
-    float g[3], f[Q];
-    body_force(L, xx, yy, z, g);  // the pair kernel runs only when g is uniform along x
-#pragma unroll
-    for (int i = 0; i < Q; ++i) f[i] = H::lo(w[i]);
-    const float ra = collide_pairs(L, f, g);
+    // Both nodes share g (the pair kernel runs only when g is uniform along x).
+    const float ga = body_amp(L, xx, yy, z);
+    float fa[Q], fb[Q];
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
-        const unsigned lo = H::bits(f[i]);
-        f[i] = H::hi(w[i]);
-        w[i] = lo;
+        const float2 v = H::unpack(w[i]);
+        fa[i] = v.x;
+        fb[i] = v.y;
     }
-    const float rb = collide_pairs(L, f, g);
+    const float ra = collide_g<FD, Store<S>::kScaled>(L, fa, ga);
+    const float rb = collide_g<FD, Store<S>::kScaled>(L, fb, ga);
     if (!isfinite(ra) || !isfinite(rb)) atomicOr(&ds->flags, FLAG_NONFINITE);
     T *dp = dst + node;
 #pragma unroll
-    for (int i = 0; i < Q; ++i, dp += plane) __stcs(reinterpret_cast<unsigned *>(dp), w[i] | (H::bits(f[i]) << 16));
+    for (int i = 0; i < Q; ++i, dp += plane) __stcs(reinterpret_cast<unsigned *>(dp), H::pack(fa[i], fb[i]));
 }
 
 // Nodes touched by atoms: redo the collision with F = g + G from the same
@@ -376,6 +409,16 @@ dim3 node_grid(const Lat &L, dim3 b) { return dim3((L.nx + b.x - 1) / b.x, (L.ny
     }                                                                                                               \
     }
 
+// Runs BODY with FDV bound at compile time to the body-force direction
+// (-1 without forcing).
+#define LBMD_FD_DISPATCH(L, BODY)                                          \
+    switch ((L).forcing == LBMD_FORCE_NONE ? -1 : (L).fdir) {             \
+        case -1: { constexpr int FDV = -1; BODY; } break;                  \
+        case 0: { constexpr int FDV = 0; BODY; } break;                    \
+        case 1: { constexpr int FDV = 1; BODY; } break;                    \
+        default: { constexpr int FDV = 2; BODY; } break;                   \
+    }
+
 cudaError_t launch_lb_step(int store, const Lat &L, void *const buf[2], DevState *ds, cudaStream_t s) {
     const bool pairs = store != LBMD_F32 && L.nx % 2 == 0 &&
                        !(L.forcing == LBMD_FORCE_KOLMOGOROV && L.faxis == 0);
@@ -386,15 +429,17 @@ cudaError_t launch_lb_step(int store, const Lat &L, void *const buf[2], DevState
         int by = 128 / bx;
         if (by > L.ny) by = L.ny;
         const dim3 b(bx, by, 1), g((half + bx - 1) / bx, (L.ny + by - 1) / by, L.nz);
-        if (store == LBMD_F16_SHIFTED)
-            k_lb_step_pair16<LBMD_F16_SHIFTED><<<g, b, 0, s>>>(L, (__half *)buf[0], (__half *)buf[1], ds);
-        else
-            k_lb_step_pair16<LBMD_BF16_SHIFTED>
-                <<<g, b, 0, s>>>(L, (__nv_bfloat16 *)buf[0], (__nv_bfloat16 *)buf[1], ds);
+        if (store == LBMD_F16_SHIFTED) {
+            LBMD_FD_DISPATCH(L, (k_lb_step_pair16<LBMD_F16_SHIFTED, FDV>
+                                 <<<g, b, 0, s>>>(L, (__half *)buf[0], (__half *)buf[1], ds)));
+        } else {
+            LBMD_FD_DISPATCH(L, (k_lb_step_pair16<LBMD_BF16_SHIFTED, FDV>
+                                 <<<g, b, 0, s>>>(L, (__nv_bfloat16 *)buf[0], (__nv_bfloat16 *)buf[1], ds)));
+        }
         return cudaGetLastError();
     }
     const dim3 b = node_block(L), g = node_grid(L, b);
-    LBMD_DISPATCH(store, (k_lb_step<SV><<<g, b, 0, s>>>(L, (T *)buf[0], (T *)buf[1], ds)));
+    LBMD_FD_DISPATCH(L, LBMD_DISPATCH(store, (k_lb_step<SV, FDV><<<g, b, 0, s>>>(L, (T *)buf[0], (T *)buf[1], ds))));
     return cudaGetLastError();
 }
 

@@ -26,7 +26,10 @@ namespace {
 thread_local std::string g_create_error;
 
 constexpr int kFold = 128;  // bucket grid per axis (cells folded modulo this)
-constexpr int kCap = 64;   // atoms per bucket
+// Atoms per bucket: a collapsed Lennard-Jones globule (sigma 0.4) packs ~30
+// atoms into a cell of side 1.3, and folding (cells 128 apart share a bucket
+// once a lattice axis holds more than 128 cells) can stack two globules.
+constexpr int kCap = 128;
 
 }  // namespace
 
@@ -145,6 +148,7 @@ std::string validate(const lbmd_params *p, int n_atoms, const double *mass, int 
     if (p->deterministic != 0) return "deterministic mode is not available";
     if (p->check_every < 0) return "check_every must be >= 0";
     if (n_atoms < 0) return "n_atoms must be >= 0";
+    if (n_atoms > (1 << 20)) return "at most 1048576 atoms (neighbour-list entries hold a 20-bit atom index)";
     if (n_bonds < 0) return "n_bonds must be >= 0";
     if (n_atoms > 0) {
         if (!mass) return "mass is NULL";
@@ -187,8 +191,6 @@ void fill_physics(lbmd_t h) {
     L.famp = (float)p.force_amp;
     L.fdir = p.force_dir;
     L.faxis = p.force_wave_axis;
-    const int nax = p.force_wave_axis == 0 ? p.nx : (p.force_wave_axis == 1 ? p.ny : p.nz);
-    L.kwave = (float)(2.0 / nax);
 
     AtomArgs &A = h->A;
     A.na = h->na;
@@ -501,6 +503,17 @@ lbmd_status lbmd_create(const lbmd_params *params, int n_atoms, const double *ma
     CREATE_CK(cudaMemsetAsync(h->C.G, 0, L.N * sizeof(float4), h->stream));
     CREATE_CK(cudaMemsetAsync(h->C.tag, 0, L.N * sizeof(int), h->stream));
     CREATE_CK(cudaMemsetAsync(h->ds, 0, sizeof(DevState), h->stream));
+    {
+        // Kolmogorov wave shape per lattice row, in FP64 then rounded once.
+        const int nax = h->p.force_wave_axis == 0 ? h->p.nx : (h->p.force_wave_axis == 1 ? h->p.ny : h->p.nz);
+        std::vector<float> shape(nax);
+        for (int c = 0; c < nax; ++c) shape[c] = (float)std::sin(6.283185307179586477 * c / nax);
+        float *d_shape;
+        CREATE_TRY(dalloc_t(h, &d_shape, (size_t)nax));
+        CREATE_CK(cudaMemcpy(d_shape, shape.data(), nax * sizeof(float), cudaMemcpyHostToDevice));
+        h->L.kshape = d_shape;
+        h->C.L.kshape = d_shape;  // the coupling kernels' copy of the lattice
+    }
 
     AtomArgs &A = h->A;
     CouplingArgs &C = h->C;

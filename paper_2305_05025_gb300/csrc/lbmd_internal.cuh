@@ -59,6 +59,10 @@ template <> struct Store<LBMD_F32> {
     static __device__ __forceinline__ float ld_plain(const T *p) { return *p; }
     static __device__ __forceinline__ void st(T *p, float v) { __stcs(p, v); }
     static __device__ __forceinline__ void st_plain(T *p, float v) { *p = v; }
+    // Stored units (the dense kernels collide in them, see collide_g).
+    static constexpr bool kScaled = false;
+    static __device__ __forceinline__ float ld_raw(const T *p) { return __ldg(p); }
+    static __device__ __forceinline__ void st_raw(T *p, float v) { __stcs(p, v); }
 };
 // FP16 holds 2^10 delta f: the exact power-of-two scale lifts the small
 // deviations of slow flows (down to ~1e-7) out of FP16's subnormal range,
@@ -70,6 +74,9 @@ template <> struct Store<LBMD_F16_SHIFTED> {
     static __device__ __forceinline__ float ld_plain(const T *p) { return __half2float(*p) * kF16Unscale; }
     static __device__ __forceinline__ void st(T *p, float v) { __stcs(p, __float2half_rn(v * kF16Scale)); }
     static __device__ __forceinline__ void st_plain(T *p, float v) { *p = __float2half_rn(v * kF16Scale); }
+    static constexpr bool kScaled = true;
+    static __device__ __forceinline__ float ld_raw(const T *p) { return __half2float(__ldg(p)); }
+    static __device__ __forceinline__ void st_raw(T *p, float v) { __stcs(p, __float2half_rn(v)); }
 };
 template <> struct Store<LBMD_BF16_SHIFTED> {
     using T = __nv_bfloat16;
@@ -77,6 +84,9 @@ template <> struct Store<LBMD_BF16_SHIFTED> {
     static __device__ __forceinline__ float ld_plain(const T *p) { return __bfloat162float(*p); }
     static __device__ __forceinline__ void st(T *p, float v) { __stcs(p, __float2bfloat16_rn(v)); }
     static __device__ __forceinline__ void st_plain(T *p, float v) { *p = __float2bfloat16_rn(v); }
+    static constexpr bool kScaled = false;
+    static __device__ __forceinline__ float ld_raw(const T *p) { return __bfloat162float(__ldg(p)); }
+    static __device__ __forceinline__ void st_raw(T *p, float v) { __stcs(p, __float2bfloat16_rn(v)); }
 };
 
 inline size_t store_bytes(int store) { return store == LBMD_F32 ? 4 : 2; }
@@ -91,17 +101,17 @@ struct Lat {
     int forcing;  // LBMD_FORCE_*
     float famp;   // body-force amplitude
     int fdir, faxis;
-    float kwave;  // 2 / n_axis (sinpi argument scale of the Kolmogorov wave)
+    const float *kshape;  // Kolmogorov wave sin(2 pi c / n_axis), c < n_axis (device table)
 };
 
-// Body force g at a node (analytic: costs no memory traffic).
+// Body force g at a node (the Kolmogorov wave from a per-row table, L1-resident).
 __device__ __forceinline__ void body_force(const Lat &L, int x, int y, int z, float g[3]) {
     g[0] = g[1] = g[2] = 0.f;
     if (L.forcing == LBMD_FORCE_NONE) return;
     float a = L.famp;
     if (L.forcing == LBMD_FORCE_KOLMOGOROV) {
         int c = L.faxis == 0 ? x : (L.faxis == 1 ? y : z);
-        a *= sinpif(L.kwave * (float)c);
+        a *= __ldg(L.kshape + c);
     }
     g[L.fdir] = a;
 }
@@ -160,14 +170,32 @@ __device__ __forceinline__ float collide(const Lat &L, float f[Q], const float F
     return rho;
 }
 
-// Same collision as collide(), evaluated per pair of opposite speeds (i odd,
-// i + 1 = -c_i) with the per-node factors hoisted: with cu = c_i.u and
-// cF = c_i.F, the new value of speed i is
-//   (1 - omega) f_i + w_i (E + O),  of its opposite  (1 - omega) f_o + w_i (E - O),
-// E = A0 + cu (9/2 omega rho cu + 9 s cF),  O = 3 omega rho cu + 3 s cF,
-// A0 = omega (drho - 3/2 rho u.u) - 3 s u.F,  s = 1 - omega/2
-// (E is the even part of the equilibrium and Guo source, O the odd part).
-__device__ __forceinline__ float collide_pairs(const Lat &L, float f[Q], const float F[3]) {
+// Amplitude a of the body force g = a e_fdir at a node (0 without forcing).
+__device__ __forceinline__ float body_amp(const Lat &L, int x, int y, int z) {
+    if (L.forcing == LBMD_FORCE_NONE) return 0.f;
+    float a = L.famp;
+    if (L.forcing == LBMD_FORCE_KOLMOGOROV) {
+        const int c = L.faxis == 0 ? x : (L.faxis == 1 ? y : z);
+        a *= __ldg(L.kshape + c);
+    }
+    return a;
+}
+
+// BGK collision + Guo source of one node whose force is the body force
+// g = ga e_FD (FD = -1: no force), specialised at compile time on FD so only
+// the speeds with a component along FD carry force terms. f holds SC times
+// the pulled deviations delta f (SC = 2^10 for FP16 storage, else 1) and
+// receives SC times the post-collision deviations. Speeds are taken with
+// their opposites: with cu = c_i.u and cF = c_i.F,
+//   new f_i = (1 - omega) f_i + SC w_i (E + O),  new f_opp = (1 - omega) f_opp + SC w_i (E - O),
+//   E = A0 + cu (9/2 omega rho cu + 9 s cF),  O = 3 omega rho cu + 3 s cF,
+//   A0 = omega (drho - 3/2 rho u.u) - 3 s u.F,  s = 1 - omega/2,
+// E the even and O the odd part of the equilibrium and the Guo source, and
+// SC w_i folded into per-class constants (faces 1/18, edges 1/36).
+// Returns rho.
+template <int FD, bool SCALED>
+__device__ __forceinline__ float collide_g(const Lat &L, float f[Q], float ga) {
+    constexpr float sc = SCALED ? kF16Scale : 1.f, isc = SCALED ? kF16Unscale : 1.f;
     float sp[9], dp[9];
 #pragma unroll
     for (int p = 0; p < 9; ++p) {
@@ -182,23 +210,45 @@ __device__ __forceinline__ float collide_pairs(const Lat &L, float f[Q], const f
         if (cy(2 * p + 1)) jy += cy(2 * p + 1) * dp[p];
         if (cz(2 * p + 1)) jz += cz(2 * p + 1) * dp[p];
     }
+    if (SCALED) {
+        drho *= isc;
+        jx *= isc;
+        jy *= isc;
+        jz *= isc;
+    }
     const float rho = L.rho0 + drho;
     const float inv = 1.f / rho;
-    const float ux = (jx + 0.5f * F[0]) * inv, uy = (jy + 0.5f * F[1]) * inv, uz = (jz + 0.5f * F[2]) * inv;
+    if (FD == 0) jx += 0.5f * ga;
+    if (FD == 1) jy += 0.5f * ga;
+    if (FD == 2) jz += 0.5f * ga;
+    const float ux = jx * inv, uy = jy * inv, uz = jz * inv;
     const float usq = ux * ux + uy * uy + uz * uz;
-    const float uF = ux * F[0] + uy * F[1] + uz * F[2];
     const float om = L.omega, s = 1.f - 0.5f * om, keep = 1.f - om;
-    const float A0 = om * (drho - 1.5f * rho * usq) - 3.f * s * uF;
-    const float k45 = 4.5f * om * rho, k3 = 3.f * om * rho, s9 = 9.f * s, s3 = 3.f * s;
-    f[0] = keep * f[0] + wgt(0) * A0;
+    const float uF = FD == 0 ? ux * ga : (FD == 1 ? uy * ga : (FD == 2 ? uz * ga : 0.f));
+    const float A0 = FD >= 0 ? om * (drho - 1.5f * rho * usq) - 3.f * s * uF : om * (drho - 1.5f * rho * usq);
+    const float orho = om * rho;
+    constexpr float wf = sc / 18.f, we = sc / 36.f;
+    const float A0f = wf * A0, A0e = we * A0;
+    const float k45f = (4.5f * wf) * orho, k45e = (4.5f * we) * orho;
+    const float k3f = (3.f * wf) * orho, k3e = (3.f * we) * orho;
+    const float sga = s * ga;
+    const float a9f = (9.f * wf) * sga, a9e = (9.f * we) * sga;
+    const float a3f = (3.f * wf) * sga, a3e = (3.f * we) * sga;
+    f[0] = keep * f[0] + (sc / 3.f) * A0;
 #pragma unroll
     for (int i = 1; i < Q; i += 2) {
+        const bool face = i <= 6;
         const float cu = cx(i) * ux + cy(i) * uy + cz(i) * uz;
-        const float cF = cx(i) * F[0] + cy(i) * F[1] + cz(i) * F[2];
-        const float E = A0 + cu * (k45 * cu + s9 * cF);
-        const float O = k3 * cu + s3 * cF;
-        f[i] = keep * f[i] + wgt(i) * (E + O);
-        f[i + 1] = keep * f[i + 1] + wgt(i) * (E - O);
+        const int cf = FD == 0 ? cx(i) : (FD == 1 ? cy(i) : (FD == 2 ? cz(i) : 0));
+        const float k45 = face ? k45f : k45e, k3 = face ? k3f : k3e, a0 = face ? A0f : A0e;
+        float t = k45 * cu, O = k3 * cu;
+        if (cf != 0) {
+            t += cf * (face ? a9f : a9e);
+            O += cf * (face ? a3f : a3e);
+        }
+        const float E = cu * t + a0;
+        f[i] = keep * f[i] + (E + O);
+        f[i + 1] = keep * f[i + 1] + (E - O);
     }
     return rho;
 }

@@ -78,6 +78,34 @@ __device__ __forceinline__ void disp_df(const AtomArgs &A, float4 pa, float4 la,
     }
 }
 
+// Neighbour-list entry: the atom index in the low kNbBits bits and, above it,
+// the wrapped difference of the two atoms' reference cells (cref_a - cref_q)
+// per axis as a 4-bit signed value. Reference cells are fixed within a
+// coupled step and lists are rebuilt at its first force evaluation, so the
+// stored differences stay valid for the whole list lifetime.
+constexpr int kNbBits = 20;
+__device__ __forceinline__ unsigned pack_nb(int q, const int dc[3]) {
+    return (unsigned)q | (((unsigned)dc[0] & 15u) << kNbBits) | (((unsigned)dc[1] & 15u) << (kNbBits + 4)) |
+           (((unsigned)dc[2] & 15u) << (kNbBits + 8));
+}
+__device__ __forceinline__ int nb_atom(unsigned e) { return (int)(e & ((1u << kNbBits) - 1u)); }
+__device__ __forceinline__ float nb_dc(unsigned e, int axis) {
+    // Move the 4-bit field to the top, then sign-extend it with an arithmetic shift.
+    return (float)((int)(e << (32 - kNbBits - 4 * (axis + 1))) >> 28);
+}
+
+// x_a - x_q for a Lennard-Jones pair from its list entry: one FP32 rounding
+// of (cell difference) h + (hi_a - hi_q) + (lo_a - lo_q), about 2^-23 of the
+// offsets, far below what FP32 inputs already fix (bonds, whose stretch
+// cancels, keep the compensated disp_df).
+__device__ __forceinline__ void disp_nb(const AtomArgs &A, float4 pa, float4 la, unsigned e, float4 pq, float4 lq,
+                                        float d[3]) {
+    const float dx = nb_dc(e, 0), dy = nb_dc(e, 1), dz = nb_dc(e, 2);
+    d[0] = fmaf(dx, A.h[0], pa.x - pq.x) + fmaf(dx, A.h_lo[0], la.x - lq.x);
+    d[1] = fmaf(dy, A.h[1], pa.y - pq.y) + fmaf(dy, A.h_lo[1], la.y - lq.y);
+    d[2] = fmaf(dz, A.h[2], pa.z - pq.z) + fmaf(dz, A.h_lo[2], la.z - lq.z);
+}
+
 // Harmonic bond force factor -k (r - r0) / r with r - r0 evaluated as
 // (r^2 - r0^2) / (r + r0) from a compensated r^2, so the stretch keeps its
 // relative precision when r is close to r0.
@@ -360,17 +388,40 @@ __global__ void k_prime_force(AtomArgs A) {
 // three slots like the buckets: kernel k reads slot g, raises g+1, clears g-1.
 
 // Builds atom a's list with the warp (27-cell search, ballot compaction).
-__device__ void build_list(const AtomArgs &A, const float4 *__restrict__ P, int g3, int a, float4 pa) {
+// Candidates are taken NBB per lane per round: all their slot loads are
+// issued together, then all their position loads, so a round costs two
+// dependent memory latencies. Bonded partners (the first 32) sit one per lane
+// and are matched with shuffles, without touching memory per candidate.
+template <int NBB, bool WRAP>
+__device__ __noinline__ void build_list(const AtomArgs &A, const float4 *__restrict__ P, int g3, int a, float4 pa, int b0,
+                           int b1) {
     const int lane = threadIdx.x & 31;
     int ca[3], cc[3];
     unpack_cref(pa.w, ca);
     current_cell(A, pa, ca, cc);
+    const int nbond = b1 - b0;
+    const int partner = lane < nbond ? A.bpart[b0 + lane] : -1;
     int bucket = 0, n = 0;
     if (lane < 27) {
-        const int ox = lane % 3 - 1, oy = (lane / 3) % 3 - 1, oz = lane / 9 - 1;
-        const int c[3] = {wrapi(cc[0] + ox, A.nc[0]), wrapi(cc[1] + oy, A.nc[1]), wrapi(cc[2] + oz, A.nc[2])};
-        bucket = bucket_of(A, c);
-        n = min(A.count[g3][bucket], A.cap);
+        const int o[3] = {lane % 3 - 1, (lane / 3) % 3 - 1, lane / 9 - 1};
+        // Skip a neighbour cell that lies wholly beyond the list radius: the
+        // gap to it along each axis is the atom's distance to the shared face
+        // (t = position within its own cell). A small margin keeps the test
+        // conservative under rounding.
+        const float pv[3] = {pa.x, pa.y, pa.z};
+        float gap2 = 0.f;
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            const float t = pv[d] - floorf(pv[d] * A.inv_h[d]) * A.h[d];
+            const float g = o[d] < 0 ? t : (o[d] > 0 ? A.h[d] - t : 0.f);
+            gap2 += g * g;
+        }
+        if (gap2 < A.rl2 * 1.0001f) {
+            const int c[3] = {wrapi(cc[0] + o[0], A.nc[0]), wrapi(cc[1] + o[1], A.nc[1]),
+                              wrapi(cc[2] + o[2], A.nc[2])};
+            bucket = bucket_of(A, c);
+            n = min(A.count[g3][bucket], A.cap);
+        }
     }
     int incl = n;
 #pragma unroll
@@ -381,29 +432,57 @@ __device__ void build_list(const AtomArgs &A, const float4 *__restrict__ P, int 
     const int total = __shfl_sync(0xffffffffu, incl, 31);
     int kept = 0;
     int *__restrict__ out = A.nbr + (size_t)a * NL_MAX;
-    for (int t = lane; t - lane < total; t += 32) {
-        int pos = 0;
+    for (int t0 = 0; t0 < total; t0 += 32 * NBB) {
+        int q[NBB];
 #pragma unroll
-        for (int step = 16; step > 0; step >>= 1) {
-            const int probe = __shfl_sync(0xffffffffu, incl, pos + step - 1);
-            if (probe <= t) pos += step;
-        }
-        const int cb = __shfl_sync(0xffffffffu, bucket, pos & 31);
-        const int before = __shfl_sync(0xffffffffu, incl - n, pos & 31);
-        bool keep = false;
-        int q = 0;
-        if (t < total) {
-            q = A.slot[g3][(size_t)cb * A.cap + (t - before)];
-            if (q != a) {
-                float d[3];
-                disp(A, pa, ca, P[q], d);
-                keep = d[0] * d[0] + d[1] * d[1] + d[2] * d[2] < A.rl2 && !bonded(A, a, q);
+        for (int u = 0; u < NBB; ++u) {
+            const int t = t0 + 32 * u + lane;
+            int pos = 0;  // cell holding candidate t: first lane whose inclusive sum exceeds t
+#pragma unroll
+            for (int step = 16; step > 0; step >>= 1) {
+                const int probe = __shfl_sync(0xffffffffu, incl, pos + step - 1);
+                if (probe <= t) pos += step;
             }
+            const int cb = __shfl_sync(0xffffffffu, bucket, pos & 31);
+            const int before = __shfl_sync(0xffffffffu, incl - n, pos & 31);
+            q[u] = t < total ? A.slot[g3][(size_t)cb * A.cap + (t - before)] : -1;
         }
-        const unsigned m = __ballot_sync(0xffffffffu, keep);
-        const int at = kept + __popc(m & ((1u << lane) - 1u));
-        if (keep && at < NL_MAX) out[at] = q;
-        kept += __popc(m);
+        float4 pq[NBB];
+#pragma unroll
+        for (int u = 0; u < NBB; ++u)
+            if (q[u] >= 0) pq[u] = P[q[u]];
+#pragma unroll
+        for (int u = 0; u < NBB; ++u) {
+            bool keep = false;
+            int dc[3] = {0, 0, 0};
+            if (q[u] >= 0 && q[u] != a) {
+                int cq[3];
+                unpack_cref(pq[u].w, cq);
+                const float pav[3] = {pa.x, pa.y, pa.z}, pqv[3] = {pq[u].x, pq[u].y, pq[u].z};
+                float r2 = 0.f;
+#pragma unroll
+                for (int d = 0; d < 3; ++d) {
+                    dc[d] = WRAP ? wrapdiff(ca[d] - cq[d], A.nc[d]) : ca[d] - cq[d];
+                    const float dd = fmaf((float)dc[d], A.h[d], pav[d] - pqv[d]);
+                    r2 += dd * dd;
+                }
+                keep = r2 < A.rl2;
+            }
+            bool is_bonded = false;
+            for (int l = 0; l < min(nbond, 32); ++l) is_bonded |= __shfl_sync(0xffffffffu, partner, l) == q[u];
+            if (keep && nbond > 32 && !is_bonded) is_bonded = bonded(A, a, q[u]);
+            keep = keep && !is_bonded;
+            // Reference cells of listed pairs are at most a few cells apart;
+            // a difference beyond the 4-bit field is reported, not stored.
+            if (keep && ((unsigned)(dc[0] + 8) | (unsigned)(dc[1] + 8) | (unsigned)(dc[2] + 8)) >= 16u) {
+                atomicOr(&A.ds->flags, FLAG_CELL);
+                keep = false;
+            }
+            const unsigned m = __ballot_sync(0xffffffffu, keep);
+            const int at = kept + __popc(m & ((1u << lane) - 1u));
+            if (keep && at < NL_MAX) out[at] = (int)pack_nb(q[u], dc);
+            kept += __popc(m);
+        }
     }
     if (lane == 0) {
         A.nnb[a] = min(kept, NL_MAX);
@@ -412,38 +491,86 @@ __device__ void build_list(const AtomArgs &A, const float4 *__restrict__ P, int 
     __syncwarp();
 }
 
-constexpr int TPA = 8;  // lanes per atom in the substep kernel
+// The substep kernel runs TPA lanes per atom and takes NB list entries per
+// lane per round (a round issues NB index loads, then NB position pairs).
+// Few atoms: 8 lanes shorten each atom's chain of dependent work; many atoms
+// (the GPU full several times over): 4 lanes spend fewer instructions on the
+// per-atom reductions.
+constexpr int NBB = 2;  // candidates per lane per round of a list build
 
-// Conservative force on atom a from its list and its bonds, over the TPA
-// lanes of its group; every lane of the group returns the full force.
-__device__ void list_force(const AtomArgs &A, const float4 *__restrict__ P, const float4 *__restrict__ Lq, int a,
-                           float4 pa, float4 la, int sub, float F[3]) {
+// A reference cell this far from every periodic boundary has no listed
+// neighbour across one (reference cells of listed pairs differ by at most a
+// few cells), so its list build can skip the minimum-image wrap.
+__device__ __forceinline__ bool near_boundary(const AtomArgs &A, const int c[3]) {
+    bool near = false;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) near = near || c[d] < 8 || c[d] > A.nc[d] - 9;
+    return near;
+}
+
+// Conservative force on atom a from its list (nn entries) and its bonds
+// (slots b0..b1), over the TPA lanes of its group; every lane of the group
+// returns the full force.
+template <int TPA, int NB>
+__device__ __forceinline__ void list_force(const AtomArgs &A, const float4 *__restrict__ P,
+                                           const float4 *__restrict__ Lq, int a, float4 pa, float4 la, int sub,
+                                           int nn, int b0, int b1, float F[3]) {
     int ca[3];
     unpack_cref(pa.w, ca);
+    // The first bond of each lane: its loads go out with the first round.
+    const int sb = b0 + sub;
+    int qb = -1;
+    float kb = 0.f, r0b = 0.f;
+    if (sb < b1) {
+        qb = A.bpart[sb];
+        kb = A.bk[sb];
+        r0b = A.br0[sb];
+    }
     float fx = 0.f, fy = 0.f, fz = 0.f;
-    const int nn = A.nnb[a];
-    const int *__restrict__ lst = A.nbr + (size_t)a * NL_MAX;
-    for (int j = sub; j < nn; j += TPA) {
-        const int q = lst[j];
-        float dh[3], dl[3];
-        disp_df(A, pa, la, ca, P[q], Lq[q], dh, dl);
-        const float d[3] = {dh[0] + dl[0], dh[1] + dl[1], dh[2] + dl[2]};
-        const float r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
-        if (r2 < A.rc2f) {
-            const float inv_r2 = 1.0f / r2;
-            const float sr2 = A.lj_sig2 * inv_r2;
-            const float sr6 = sr2 * sr2 * sr2;
-            const float fr = A.lj_24eps * inv_r2 * sr6 * (2.f * sr6 - 1.f) - A.lj_fc * rsqrtf(r2);
-            fx += fr * d[0];
-            fy += fr * d[1];
-            fz += fr * d[2];
+    const unsigned *__restrict__ lst = reinterpret_cast<const unsigned *>(A.nbr) + (size_t)a * NL_MAX;
+    for (int j0 = sub; j0 < nn; j0 += TPA * NB) {
+        unsigned e[NB];
+#pragma unroll
+        for (int u = 0; u < NB; ++u) {
+            const int j = j0 + u * TPA;
+            e[u] = j < nn ? lst[j] : 0u;
+        }
+        float4 ph[NB], pl[NB];
+#pragma unroll
+        for (int u = 0; u < NB; ++u)
+            if (j0 + u * TPA < nn) {
+                const int q = nb_atom(e[u]);
+                ph[u] = P[q];
+                pl[u] = Lq[q];
+            }
+#pragma unroll
+        for (int u = 0; u < NB; ++u) {
+            if (j0 + u * TPA >= nn) continue;
+            float d[3];
+            disp_nb(A, pa, la, e[u], ph[u], pl[u], d);
+            const float r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+            if (r2 < A.rc2f) {
+                const float inv_r2 = 1.0f / r2;
+                const float sr2 = A.lj_sig2 * inv_r2;
+                const float sr6 = sr2 * sr2 * sr2;
+                const float fr = A.lj_24eps * inv_r2 * sr6 * (2.f * sr6 - 1.f) - A.lj_fc * rsqrtf(r2);
+                fx += fr * d[0];
+                fy += fr * d[1];
+                fz += fr * d[2];
+            }
         }
     }
-    for (int s = A.bstart[a] + sub; s < A.bstart[a + 1]; s += TPA) {
-        const int q = A.bpart[s];
+    for (int s = sb; s < b1; s += TPA) {
+        int q = qb;
+        float k = kb, r0 = r0b;
+        if (s != sb) {
+            q = A.bpart[s];
+            k = A.bk[s];
+            r0 = A.br0[s];
+        }
         float dh[3], dl[3];
         disp_df(A, pa, la, ca, P[q], Lq[q], dh, dl);
-        const float fr = bond_factor(dh, dl, A.bk[s], A.br0[s]);
+        const float fr = bond_factor(dh, dl, k, r0);
         fx += fr * (dh[0] + dl[0]);
         fy += fr * (dh[1] + dl[1]);
         fz += fr * (dh[2] + dl[2]);
@@ -465,11 +592,16 @@ __device__ __forceinline__ float4 shfl4(float4 v, int src) {
 }
 
 // TPA lanes per atom, atoms in warp-sorted order (neighbouring warps touch
-// neighbouring atoms). When the flag of this generation is up the warp first
-// rebuilds the lists of its atoms one after the other (all 32 lanes on each);
-// then each group evaluates its atom's force over the list, lanes 0-2 of the
-// group integrate one component each, and lane 0 re-bins the atom.
-__global__ void __launch_bounds__(128) k_md_substep(AtomArgs A, int k) {
+// neighbouring atoms). Every load that depends only on the atom index is
+// issued at once, before any store, so a substep costs few dependent memory
+// latencies: the device step and flags, the atom index, the atom's state,
+// two per round of its list, and the bucket insertion. When the flag of this
+// generation is up the warp first rebuilds the lists of its atoms one after
+// the other (all 32 lanes on each); then each group evaluates its atom's
+// force over the list, lanes 0-2 of the group integrate one component each,
+// and lane 0 re-bins the atom.
+template <int TPA, int NB>
+__global__ void __launch_bounds__(128, TPA == 8 ? 9 : 8) k_md_substep(AtomArgs A, int k) {
     // With programmatic dependent launch this kernel may start before the
     // previous substep has finished: wait for its results first.
     cudaGridDependencySynchronize();
@@ -478,27 +610,40 @@ __global__ void __launch_bounds__(128) k_md_substep(AtomArgs A, int k) {
     const int slot = ((blockIdx.x * blockDim.x + threadIdx.x) >> 5) * (32 / TPA) + lane / TPA;
     const int na = A.na;
     const int step = A.ds->step;
+    const int fl0 = A.ds->nl_flag[0], fl1 = A.ds->nl_flag[1], fl2 = A.ds->nl_flag[2];
+    const int warp_first = slot - lane / TPA;
+    const int a = warp_first < na ? A.order[slot < na ? slot : warp_first] : 0;
     const int g3 = ((step % 3) * (A.n_md % 3) + k) % 3;
     const int gn3 = (g3 + 1) % 3, gp3 = (g3 + 2) % 3;
     const int par = ((step & 1) * (A.n_md & 1) + k) & 1;
-    const int rebuild = A.ds->nl_flag[g3];
+    const int rebuild = g3 == 0 ? fl0 : (g3 == 1 ? fl1 : fl2);
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         A.ds->nl_flag[gp3] = 0;
-        // Kernel 0 evaluates no force: hand a pending rebuild on to kernel 1.
-        if (k == 0 && rebuild) atomicOr(&A.ds->nl_flag[gn3], 1);
+        // Kernel 0 evaluates no force. The reference cells were reset for this
+        // coupled step, so kernel 1 rebuilds every list (their entries hold
+        // reference-cell differences).
+        if (k == 0) atomicOr(&A.ds->nl_flag[gn3], 1);
     }
-    const int warp_first = slot - lane / TPA;
     if (warp_first >= na) return;  // whole warp past the end
     const bool valid = slot < na;
-    const int a = A.order[valid ? slot : warp_first];
-    // Issue the integration loads early: lane d < 3 of the group owns
-    // component d.
+    // Everything that depends only on a, in one go: lane d < 3 of the group
+    // owns component d.
     const int dcomp = sub < 3 ? sub : 0;
     const float vd = A.V[dcomp * na + a], Ud = A.U[dcomp * na + a];
     const float Jd = k == 0 ? 0.f : A.J[dcomp * na + a];
+    const float Dold = A.D[dcomp * na + a];
     const float im = A.inv_m[a];
     const float4 pa = A.P[par][a];
     const float4 la = A.L[par][a];
+    const int nn = A.nnb[a];
+    const int b0 = A.bstart[a], b1 = A.bstart[a + 1];
+    const int old_bucket = sub == 0 && k < A.n_md ? A.bucket[gp3][a] : 0;
+    float F[3] = {0.f, 0.f, 0.f};
+    if (k == 0) {
+        F[0] = A.F[a];
+        F[1] = A.F[na + a];
+        F[2] = A.F[2 * na + a];
+    }
     if (A.recP && valid) {
         if (sub == 0) {
             A.recP[(size_t)k * na + a] = pa;
@@ -506,23 +651,28 @@ __global__ void __launch_bounds__(128) k_md_substep(AtomArgs A, int k) {
         }
         if (sub < 3) A.recV[(size_t)k * 3 * na + sub * na + a] = vd;
     }
-    float F[3];
-    if (k == 0) {
-        F[0] = A.F[a];
-        F[1] = A.F[na + a];
-        F[2] = A.F[2 * na + a];
-    } else {
-        if (rebuild) {
+    const bool reset = k > 0 && rebuild;
+    if (k > 0) {
+        int nlist = nn;
+        if (reset) {
             for (int g = 0; g < 32 / TPA; ++g) {
                 const int ag = __shfl_sync(0xffffffffu, a, g * TPA);
                 const int vg = __shfl_sync(0xffffffffu, (int)valid, g * TPA);
+                const int bg0 = __shfl_sync(0xffffffffu, b0, g * TPA), bg1 = __shfl_sync(0xffffffffu, b1, g * TPA);
                 const float4 pg = shfl4(pa, g * TPA);
-                if (vg) build_list(A, A.P[par], g3, ag, pg);
+                if (vg) {
+                    int cg[3];
+                    unpack_cref(pg.w, cg);
+                    if (near_boundary(A, cg))
+                        build_list<NBB, true>(A, A.P[par], g3, ag, pg, bg0, bg1);
+                    else
+                        build_list<NBB, false>(A, A.P[par], g3, ag, pg, bg0, bg1);
+                }
             }
-            if (valid && sub < 3) A.D[sub * na + a] = 0.f;
             __syncwarp();
+            nlist = A.nnb[a];
         }
-        list_force(A, A.P[par], A.L[par], a, pa, la, sub, F);
+        list_force<TPA, NB>(A, A.P[par], A.L[par], a, pa, la, sub, nlist, b0, b1, F);
     }
     if (!valid) return;
     // Lanes 0-2: one velocity-Verlet component each.
@@ -549,7 +699,9 @@ __global__ void __launch_bounds__(128) k_md_substep(AtomArgs A, int k) {
             two_sum(p, inc, s, e_add);
             p = s;
             lo += e_add + e_mul;
-            Dd = A.D[sub * na + a] + inc;
+            // Drift since the last list build (which this kernel just did
+            // when reset is set).
+            Dd = (reset ? 0.f : Dold) + inc;
             A.D[sub * na + a] = Dd;
         } else {
             // End of the coupled step: cache the force and advance the FP64
@@ -558,13 +710,14 @@ __global__ void __launch_bounds__(128) k_md_substep(AtomArgs A, int k) {
             const float lc = sub == 0 ? la.x : (sub == 1 ? la.y : la.z);
             A.F[sub * na + a] = Fd;
             A.X[sub * na + a] += ((double)pc - (double)A.P0[sub * na + a]) + ((double)lc - (double)A.R0[sub * na + a]);
+            if (reset) A.D[sub * na + a] = 0.f;
         }
         A.V[sub * na + a] = v;
         A.J[sub * na + a] = J;
     }
     if (k == A.n_md) return;
     const int base = lane & ~(TPA - 1);
-    const unsigned gm = 0xffu << base;  // this group's lanes (valid groups are whole)
+    const unsigned gm = (TPA == 32 ? 0xffffffffu : ((1u << TPA) - 1u)) << base;  // valid groups are whole
     const float px = __shfl_sync(gm, p, base), py = __shfl_sync(gm, p, base + 1), pz = __shfl_sync(gm, p, base + 2);
     const float lx = __shfl_sync(gm, lo, base), ly = __shfl_sync(gm, lo, base + 1), lz = __shfl_sync(gm, lo, base + 2);
     const float D2 = __shfl_sync(gm, Dd * Dd, base) + __shfl_sync(gm, Dd * Dd, base + 1) +
@@ -573,7 +726,7 @@ __global__ void __launch_bounds__(128) k_md_substep(AtomArgs A, int k) {
     const float4 pn = make_float4(px, py, pz, pa.w);
     A.P[par ^ 1][a] = pn;
     A.L[par ^ 1][a] = make_float4(lx, ly, lz, 0.f);
-    A.count[gp3][A.bucket[gp3][a]] = 0;
+    A.count[gp3][old_bucket] = 0;
     int cr[3], c[3];
     unpack_cref(pa.w, cr);
     current_cell(A, pn, cr, c);
@@ -649,10 +802,10 @@ cudaError_t launch_md_prime(const AtomArgs &a, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-cudaError_t launch_md_substep(const AtomArgs &a, int k, cudaStream_t s) {
-    if (a.na == 0) return cudaSuccess;
+template <int TPA>
+cudaError_t launch_substep(const AtomArgs &a, int k, cudaStream_t s) {
     cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3((a.na + 4 * (32 / TPA) - 1) / (4 * (32 / TPA)));  // TPA lanes per atom
+    cfg.gridDim = dim3((a.na + 4 * (32 / TPA) - 1) / (4 * (32 / TPA)));  // 128 threads, TPA lanes per atom
     cfg.blockDim = dim3(128);
     cfg.stream = s;
     cudaLaunchAttribute attr[1];
@@ -660,7 +813,13 @@ cudaError_t launch_md_substep(const AtomArgs &a, int k, cudaStream_t s) {
     attr[0].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, k_md_substep, a, k);
+    return cudaLaunchKernelEx(&cfg, k_md_substep<TPA, 2>, a, k);
+}
+
+cudaError_t launch_md_substep(const AtomArgs &a, int k, cudaStream_t s) {
+    if (a.na == 0) return cudaSuccess;
+    // Above ~64k atoms the 8-lane grid no longer fits the GPU in one wave.
+    return a.na > 65536 ? launch_substep<4>(a, k, s) : launch_substep<8>(a, k, s);
 }
 
 cudaError_t launch_md_sort(const AtomArgs &a, cudaStream_t s) {

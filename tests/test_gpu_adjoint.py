@@ -98,3 +98,34 @@ def test_autograd_function_returns_adjoint_gradients():
     assert np.isclose(g.grad.item(), 2 * dg, rtol=1e-6)
     assert np.isclose(t.grad.item(), 2 * dtau, rtol=1e-6)
     assert np.isclose(a.grad.item(), 2 * da, rtol=1e-6)
+
+
+def test_adjoint_full_size_matches_gpu_fd_chain5k_lattice64():
+    """The adjoint workload at full size (64^3, 5,000-bead globule, uniform
+    forcing 1e-5, 200 steps, checkpoints every 20) with harmonic bonds only:
+    the Lennard-Jones globule is chaotic over 200 steps, so its exact
+    derivative is dominated by exponential growth and has no converged finite
+    difference. The adjoint must equal the Richardson central difference of
+    the GPU's own forward observable (the same arithmetic it differentiates)."""
+    cfg = synth.workload("chain5k_lattice64_uniform", lj_eps=0.0, n_md=128, skin=0.3)
+    inp = synth.inputs(cfg, 1)
+    steps, ckpt = cfg["steps"], cfg["ckpt_every"]
+    h = make(cfg, inp)
+    obs, dg, dtau, da = lbmd.lbmd_backward(h, steps, ckpt, lbmd.OBS_DRAG_X)
+    lbmd.lbmd_destroy(h)
+    got = dict(gamma=dg, tau=dtau, force_amp=da)
+
+    def gpu_obs(key, value):
+        hh = make(dict(cfg, **{key: value}), inp)
+        o = lbmd.lbmd_backward(hh, steps, ckpt, lbmd.OBS_DRAG_X)[0]
+        lbmd.lbmd_destroy(hh)
+        return o
+
+    for key, rel in (("gamma", 1e-2), ("tau", 1e-2), ("force_amp", 1e-2)):
+        x0 = cfg[key]
+        hstep = rel * abs(x0)
+        d1 = (gpu_obs(key, x0 + hstep) - gpu_obs(key, x0 - hstep)) / (2 * hstep)
+        d2 = (gpu_obs(key, x0 + hstep / 2) - gpu_obs(key, x0 - hstep / 2)) / hstep
+        ref, spread = (4 * d2 - d1) / 3, abs(d2 - d1)
+        print(f"chain5k 64^3 200 steps d/d{key}: adjoint {got[key]:.8e} GPU FD {ref:.8e} (spread {spread:.1e})")
+        assert abs(got[key] - ref) <= 1e-3 * abs(ref) + 3 * spread, key

@@ -6,7 +6,8 @@ bench.py times (one CUDA graph per step, n_md = 128, gamma = 0.05, skin 0.3):
 - 256^3 / 60k-bead trimer: one step in FP32, FP16 and BF16 storage against the
   oracle, with the per-field error table (f - w rho0, rho - rho0, u, x, v);
 - 512^3 z-channel with ten globules: FP32 and FP16 storage run, no flag
-  raised, mass kept, and the FP16-vs-FP32 difference per field."""
+  raised, mass kept, and the FP16-vs-FP32 difference per field after one
+  step."""
 import numpy as np
 import pytest
 
@@ -108,6 +109,10 @@ def test_trimer60k_lattice256_storage_formats(orc):
 
 
 def test_channel10x20k_lattice512_runs():
+    """FP16 against FP32 storage after one coupled step (the dense collapsing
+    globules are chaotic: a second step already amplifies the storage
+    difference in the atom positions by orders of magnitude), then one more
+    step each with no flag raised and mass kept."""
     cfg32 = synth.workload("channel10x20k_lattice512", **BENCH)
     inp = synth.inputs(cfg32, 1)
     res = {}
@@ -115,13 +120,19 @@ def test_channel10x20k_lattice512_runs():
         cfg = dict(cfg32, store=store)
         h = make(cfg, inp)
         m0, _, _ = lbmd.lbmd_get_stats(h)
-        lbmd.lbmd_step(h, 2)
+        lbmd.lbmd_step(h, 1)
+        lbmd.lbmd_check(h)
+        res[store] = lbmd.lbmd_get_fields(h, u=True, x=True, v=True)
+        lbmd.lbmd_step(h, 1)
         lbmd.lbmd_check(h)
         m1, _, _ = lbmd.lbmd_get_stats(h)
         assert abs(m1 - m0) < 1e-7 * m0, (store, m1 - m0)
-        res[store] = lbmd.lbmd_get_fields(h, u=True, x=True, v=True)
         lbmd.lbmd_destroy(h)
-    for k in ("u", "x", "v"):
+    # FP16 resolution of delta f (2^-11 relative) in u; x and v see it only
+    # through the friction with the interpolated u.
+    bounds = dict(u=1e-2, x=1e-6, v=2e-3)
+    for k, b in bounds.items():
         e = rel_linf(res["f16"][k], res["f32"][k])
-        print(f"512^3 channel FP16 vs FP32 {k}: rel Linf {e:.2e}, max |FP32| {np.abs(res['f32'][k]).max():.2e}")
-        assert e < (2e-2 if k != "x" else 1e-6)  # FP16 storage resolution, amplified by the chaotic solute
+        print(f"512^3 channel FP16 vs FP32 after one step, {k}: rel Linf {e:.2e}, "
+              f"max |FP32| {np.abs(res['f32'][k]).max():.2e}")
+        assert e < b, (k, e)
