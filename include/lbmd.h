@@ -108,8 +108,7 @@ typedef struct {
  * the topology. mass: n_atoms masses (> 0). bonds: 2*n_bonds atom indices;
  * bond_k, bond_r0: n_bonds stiffnesses and rest lengths (U = k (r - r0)^2/2).
  * Bonded pairs are excluded from the Lennard-Jones sum. n_atoms may be 0 (a
- * lattice-only run) and at most 2^20 = 1,048,576 (neighbour-list entries pack
- * a 20-bit atom index). cuda_stream: a cudaStream_t (NULL: the legacy default
+ * lattice-only run). cuda_stream: a cudaStream_t (NULL: the legacy default
  * stream). Host pointers. On failure *out is NULL. */
 lbmd_status lbmd_create(const lbmd_params *params, int n_atoms, const double *mass, int n_bonds,
                         const int32_t *bonds, const double *bond_k, const double *bond_r0,

@@ -191,15 +191,11 @@ __global__ void k_adj_md_local(AdjArgs D, AtomArgs A, CouplingArgs C, int k) {
 __global__ void k_adj_bins(AtomArgs A, int k) {
     const int a = blockIdx.x * blockDim.x + threadIdx.x;
     if (a >= A.na) return;
-    const float4 pa = A.recP[(size_t)k * A.na + a];
-    int cr[3], c[3];
-    cr[0] = (int)(__float_as_uint(pa.w) & 1023u);
-    cr[1] = (int)((__float_as_uint(pa.w) >> CREF_BITS) & 1023u);
-    cr[2] = (int)((__float_as_uint(pa.w) >> (2 * CREF_BITS)) & 1023u);
-    const float pp[3] = {pa.x, pa.y, pa.z};
+    const float4 pa = A.recP[(size_t)k * A.na + a], la = A.recL[(size_t)k * A.na + a];
+    const float v[3] = {(pa.x - A.off[0]) + la.x, (pa.y - A.off[1]) + la.y, (pa.z - A.off[2]) + la.z};
+    int c[3];
     for (int d = 0; d < 3; ++d) {
-        int cc = cr[d] + (int)floorf(pp[d] * A.inv_h[d]);
-        cc %= A.nc[d];
+        int cc = (int)floorf(v[d] * A.inv_h[d]) % A.nc[d];
         c[d] = cc < 0 ? cc + A.nc[d] : cc;
     }
     const int b = ((c[2] & A.fmask[2]) * A.fold[1] + (c[1] & A.fmask[1])) * A.fold[0] + (c[0] & A.fmask[0]);
@@ -210,30 +206,15 @@ __global__ void k_adj_bins(AtomArgs A, int k) {
         atomicOr(&A.ds->flags, FLAG_CELL);
 }
 
-__device__ __forceinline__ int wrapdiff_a(int d, int n) {
-    if (2 * d > n) return d - n;
-    if (2 * d < -n) return d + n;
-    return d;
-}
-
-__device__ __forceinline__ void two_sum_a(float a, float b, float &s, float &e) {
-    s = a + b;
-    const float bp = s - a;
-    e = (a - (s - bp)) + (b - bp);
-}
-
-// x_a - x_b at the recorded positions (hi + lo parts, error-free sums).
+// x_a - x_b at the recorded positions: in the step frame the hi difference
+// and the fold by whole box lengths are exact, the lo parts add below FP32
+// resolution.
 __device__ __forceinline__ void rec_disp(const AtomArgs &A, float4 pa, float4 la, float4 pb, float4 lb, float d[3]) {
-    const unsigned ua = __float_as_uint(pa.w), ub = __float_as_uint(pb.w);
     const float ha[3] = {pa.x, pa.y, pa.z}, hb[3] = {pb.x, pb.y, pb.z};
     const float la3[3] = {la.x, la.y, la.z}, lb3[3] = {lb.x, lb.y, lb.z};
     for (int k = 0; k < 3; ++k) {
-        const int ca = (int)((ua >> (CREF_BITS * k)) & 1023u), cb = (int)((ub >> (CREF_BITS * k)) & 1023u);
-        const float dc = (float)wrapdiff_a(ca - cb, A.nc[k]);
-        float s, e, s2, e2;
-        two_sum_a(ha[k], -hb[k], s, e);
-        two_sum_a(dc * A.h[k], s, s2, e2);
-        d[k] = s2 + ((e + e2) + ((la3[k] - lb3[k]) + dc * A.h_lo[k]));
+        const float s = ha[k] - hb[k];
+        d[k] = fmaf(-A.Lf[k], rintf(s * A.inv_Lf[k]), s) + (la3[k] - lb3[k]);
     }
 }
 
@@ -266,15 +247,13 @@ __global__ void __launch_bounds__(128) k_adj_hvp(AdjArgs D, AtomArgs A, int k) {
     const int b0 = A.bstart[a], b1 = A.bstart[a + 1];
     const int nbond = b1 - b0;
     const int partner = lane < nbond ? A.bpart[b0 + lane] : -1;
-    const unsigned ua = __float_as_uint(pa.w);
-    const float pp[3] = {pa.x, pa.y, pa.z};
+    const float pp[3] = {(pa.x - A.off[0]) + la.x, (pa.y - A.off[1]) + la.y, (pa.z - A.off[2]) + la.z};
     int cc[3];
     float t[3];  // position within the current cell
     for (int d = 0; d < 3; ++d) {
-        const int cr = (int)((ua >> (CREF_BITS * d)) & 1023u);
         const float fl = floorf(pp[d] * A.inv_h[d]);
         t[d] = pp[d] - fl * A.h[d];
-        int c = (cr + (int)fl) % A.nc[d];
+        int c = (int)fl % A.nc[d];
         cc[d] = c < 0 ? c + A.nc[d] : c;
     }
     int bucket = 0, n = 0;
@@ -285,7 +264,7 @@ __global__ void __launch_bounds__(128) k_adj_hvp(AdjArgs D, AtomArgs A, int k) {
             const float g = o[d] < 0 ? t[d] : (o[d] > 0 ? A.h[d] - t[d] : 0.f);
             gap2 += g * g;
         }
-        if (gap2 < A.rc2f * 1.0001f) {
+        if (gap2 < A.rc2f * 1.001f) {
             int c[3];
             for (int d = 0; d < 3; ++d) {
                 const int v = (cc[d] + o[d]) % A.nc[d];

@@ -12,8 +12,8 @@ __device__ __forceinline__ int wrapl(long long c, int n) {
     return (int)(r < 0 ? r + n : r);
 }
 
-// Start of a coupled step, one thread per atom: set the atom's FP32 reference
-// frame for the substeps, build its trilinear stencil from the FP64 position,
+// Start of a coupled step, one thread per atom: set the atom's FP32 step frame
+// for the substeps, build its trilinear stencil from the FP64 position,
 // interpolate u = (sum f c + g/2)/rho over the eight corners (pulled from the
 // current post-collision buffer), and claim the corners in the touched-node
 // list (each node enters once per step).
@@ -28,28 +28,12 @@ __global__ void __launch_bounds__(128) k_interp(CouplingArgs C, AtomArgs A, cons
     const int par = (int)(((long long)step * A.n_md) & 1);
     const Lat &L = C.L;
 
-    double x[3];
-    bool finite = true;
-    int cr[3];
-    float p0[3], r0[3];
-    for (int d = 0; d < 3; ++d) {
-        x[d] = C.X[d * na + a];
-        finite = finite && isfinite(x[d]);
-        const double s = x[d] * ((double)A.nc[d] / A.Ld[d]);
-        double fl = floor(s);
-        if (!(fabs(fl) < 4.0e15)) fl = 0.0;
-        cr[d] = wrapl((long long)fl, A.nc[d]);
-        const double off = (s - fl) * A.hd[d];
-        p0[d] = (float)off;
-        r0[d] = (float)(off - (double)p0[d]);
-        A.P0[d * na + a] = p0[d];
-        A.R0[d * na + a] = r0[d];
-    }
-    A.P[par][a] = make_float4(p0[0], p0[1], p0[2],
-                              __uint_as_float((unsigned)cr[0] | ((unsigned)cr[1] << CREF_BITS) |
-                                              ((unsigned)cr[2] << (2 * CREF_BITS))));
-    A.L[par][a] = make_float4(r0[0], r0[1], r0[2], 0.f);
+    float4 fp, fl4;
+    const bool finite = set_frame(A, a, fp, fl4);
+    A.P[par][a] = fp;
+    A.L[par][a] = fl4;
     if (!finite) atomicOr(&C.ds->flags, FLAG_NONFINITE);
+    const double x[3] = {C.X[a], C.X[na + a], C.X[2 * na + a]};
 
     int b[3];
     float t[3];

@@ -137,7 +137,7 @@ __device__ __forceinline__ void pull_pair(const typename Store<S>::T *sp, ptrdif
 // neighbouring lane's word (or one 16-bit load at a row or warp edge), and
 // both results leave as one 32-bit store.
 template <int S, int FD>
-__global__ void __launch_bounds__(128, 7) k_lb_step_pair16(Lat L, typename Store<S>::T *b0, typename Store<S>::T *b1,
+__global__ void __launch_bounds__(128, 8) k_lb_step_pair16(Lat L, typename Store<S>::T *b0, typename Store<S>::T *b1,
                                                         DevState *ds) {
     using T = typename Store<S>::T;
     using H = Half16<S>;

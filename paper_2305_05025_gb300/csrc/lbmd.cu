@@ -148,7 +148,6 @@ std::string validate(const lbmd_params *p, int n_atoms, const double *mass, int 
     if (p->deterministic != 0) return "deterministic mode is not available";
     if (p->check_every < 0) return "check_every must be >= 0";
     if (n_atoms < 0) return "n_atoms must be >= 0";
-    if (n_atoms > (1 << 20)) return "at most 1048576 atoms (neighbour-list entries hold a 20-bit atom index)";
     if (n_bonds < 0) return "n_bonds must be >= 0";
     if (n_atoms > 0) {
         if (!mass) return "mass is NULL";
@@ -163,7 +162,6 @@ std::string validate(const lbmd_params *p, int n_atoms, const double *mass, int 
         for (int d = 0; d < 3; ++d) {
             const int nc = (int)std::floor((double)L[d] / side);
             if (nc < 3) return "each box side must hold at least 3 pair-search cells (side >= 3 (rcut + skin))";
-            if (nc > 1023) return "at most 1023 pair-search cells per axis";
         }
     }
     if (n_bonds > 0) {
@@ -216,7 +214,12 @@ void fill_physics(lbmd_t h) {
         A.hd[d] = (double)Ls[d] / A.nc[d];
         A.h[d] = (float)A.hd[d];
         A.inv_h[d] = (float)(A.nc[d] / (double)Ls[d]);
-        A.h_lo[d] = (float)(A.hd[d] - (double)A.h[d]);
+        A.Lf[d] = (float)Ls[d];
+        A.inv_Lf[d] = (float)(1.0 / Ls[d]);
+        double B = 1.0;
+        while (B < 2.0 * Ls[d]) B *= 2.0;
+        A.offd[d] = B + 0.5 * (B - Ls[d]);
+        A.off[d] = (float)A.offd[d];
     }
     A.cap = kCap;
     h->C.L = L;

@@ -234,21 +234,37 @@ __device__ __forceinline__ float collide_g(const Lat &L, float f[Q], float ga) {
     const float sga = s * ga;
     const float a9f = (9.f * wf) * sga, a9e = (9.f * we) * sga;
     const float a3f = (3.f * wf) * sga, a3e = (3.f * we) * sga;
+    // E + O = (A0 + cF a3) + cu (k45 cu + cF a9 + k3), E - O likewise with -k3
+    // and -a3: per class and sign of c_i.F, two nested FMAs per result.
+    const float Ppf = a9f + k3f, Pmf = a9f - k3f, Qpf = A0f + a3f, Qmf = A0f - a3f;
+    const float Ppe = a9e + k3e, Pme = a9e - k3e, Qpe = A0e + a3e, Qme = A0e - a3e;
     f[0] = keep * f[0] + (sc / 3.f) * A0;
 #pragma unroll
     for (int i = 1; i < Q; i += 2) {
         const bool face = i <= 6;
         const float cu = cx(i) * ux + cy(i) * uy + cz(i) * uz;
         const int cf = FD == 0 ? cx(i) : (FD == 1 ? cy(i) : (FD == 2 ? cz(i) : 0));
-        const float k45 = face ? k45f : k45e, k3 = face ? k3f : k3e, a0 = face ? A0f : A0e;
-        float t = k45 * cu, O = k3 * cu;
-        if (cf != 0) {
-            t += cf * (face ? a9f : a9e);
-            O += cf * (face ? a3f : a3e);
+        const float k45 = face ? k45f : k45e;
+        float inP, inM, outP, outM;  // E + O = fma(cu, fma(k45, cu, inP), outP), E - O with inM, outM
+        if (cf == 0) {
+            inP = face ? k3f : k3e;
+            inM = -inP;
+            outP = outM = face ? A0f : A0e;
+        } else if (cf > 0) {
+            inP = face ? Ppf : Ppe;
+            inM = face ? Pmf : Pme;
+            outP = face ? Qpf : Qpe;
+            outM = face ? Qmf : Qme;
+        } else {
+            inP = -(face ? Pmf : Pme);
+            inM = -(face ? Ppf : Ppe);
+            outP = face ? Qmf : Qme;
+            outM = face ? Qpf : Qpe;
         }
-        const float E = cu * t + a0;
-        f[i] = keep * f[i] + (E + O);
-        f[i + 1] = keep * f[i + 1] + (E - O);
+        const float EpO = fmaf(cu, fmaf(k45, cu, inP), outP);
+        const float EmO = fmaf(cu, fmaf(k45, cu, inM), outM);
+        f[i] = fmaf(keep, f[i], EpO);
+        f[i + 1] = fmaf(keep, f[i + 1], EmO);
     }
     return rho;
 }
@@ -275,13 +291,14 @@ __device__ __forceinline__ float node_velocity(const Lat &L, const float f[Q], c
 // Atoms.
 //
 // Positions: X (FP64, unwrapped) is the accumulator, advanced once per coupled
-// step. Inside a step each atom carries its offset from the corner of a
-// reference cell cref (fixed for the step) as an unevaluated FP32 pair
-// hi + lo, advanced with error-free (two-sum) updates, so a pair displacement
-// d = wrap(cref_a - cref_b) h + (hi_a - hi_b) + (lo_a - lo_b) carries ~2^-44
-// relative error before its final rounding.
+// step. Inside a step each atom carries its periodic image in the step frame,
+// origin + (x mod L) with origin = B + (B - L)/2 and B the smallest power of
+// two >= 2L, as an unevaluated FP32 pair hi + lo advanced with error-free
+// (two-sum) updates. Every hi lies in the binade [B, 2B) (margins of at least
+// L/2 absorb the drift within a step), where differences of hi values and
+// folds by whole box lengths are exact: a pair displacement
+// (hi_a - hi_b) - k L + (lo_a - lo_b) carries one final FP32 rounding.
 
-constexpr int CREF_BITS = 10;  // cref packs three cell coordinates < 1024
 constexpr int kMortonBits = 7;                              // bucket coordinates < 128
 constexpr int kMortonCodes = 1 << (3 * kMortonBits);       // 2^21 Morton codes
 constexpr int NL_MAX = 256;    // neighbour-list capacity per atom (close packing of sigma = 0.4 beads within 1.3: ~200)
@@ -298,11 +315,13 @@ struct AtomArgs {
     int cap;              // slots per bucket
     float h[3], inv_h[3];
     double hd[3], Ld[3];
+    float Lf[3], inv_Lf[3];  // box lengths and their inverses
+    float off[3];         // step-frame origin per axis (exact in FP32)
+    double offd[3];
     double *X;            // 3*na FP64 accumulator
-    float4 *P[2];         // (hi x, hi y, hi z, cref bits) by substep parity
+    float4 *P[2];         // (hi x, hi y, hi z, 0) by substep parity
     float4 *L[2];         // (lo x, lo y, lo z, 0) by substep parity
     float *P0, *R0;       // 3*na step-start hi and lo parts
-    float h_lo[3];        // hd - (double)h
     float *V, *F, *U, *J; // 3*na SoA each
     float *mass, *inv_m;
     const int *bstart, *bpart;  // bond CSR
@@ -321,6 +340,28 @@ struct AtomArgs {
     int *scan_block;      // kMortonCodes / 1024 block offsets
     DevState *ds;
 };
+
+// Step frame of an atom from its FP64 position: the periodic image in
+// [0, L) shifted by the frame origin into the binade [B, 2B), split into
+// hi + lo. Also the step-start copies used to advance X at the step's end.
+__device__ __forceinline__ bool set_frame(const AtomArgs &A, int a, float4 &p, float4 &l) {
+    bool finite = true;
+    float hi[3], lo[3];
+    for (int d = 0; d < 3; ++d) {
+        const double x = A.X[d * A.na + a];
+        finite = finite && isfinite(x);
+        double w = x - floor(x / A.Ld[d]) * A.Ld[d];
+        if (!(w >= 0.0 && w < A.Ld[d])) w = 0.0;  // non-finite or rounding at the top edge
+        const double y = A.offd[d] + w;
+        hi[d] = (float)y;
+        lo[d] = (float)(y - (double)hi[d]);
+        A.P0[d * A.na + a] = hi[d];
+        A.R0[d * A.na + a] = lo[d];
+    }
+    p = make_float4(hi[0], hi[1], hi[2], 0.f);
+    l = make_float4(lo[0], lo[1], lo[2], 0.f);
+    return finite;
+}
 
 struct CouplingArgs {
     Lat L;

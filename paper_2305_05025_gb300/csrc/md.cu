@@ -27,89 +27,54 @@ __device__ __forceinline__ int wrapi(int c, int n) {
     return r < 0 ? r + n : r;
 }
 
-__device__ __forceinline__ void unpack_cref(float w, int c[3]) {
-    const unsigned u = __float_as_uint(w);
-    c[0] = (int)(u & 1023u);
-    c[1] = (int)((u >> CREF_BITS) & 1023u);
-    c[2] = (int)((u >> (2 * CREF_BITS)) & 1023u);
-}
-
-__device__ __forceinline__ float pack_cref(const int c[3]) {
-    return __uint_as_float((unsigned)c[0] | ((unsigned)c[1] << CREF_BITS) | ((unsigned)c[2] << (2 * CREF_BITS)));
-}
-
-// Nearest periodic image of a cell-index difference.
-__device__ __forceinline__ int wrapdiff(int d, int n) {
-    if (2 * d > n) return d - n;
-    if (2 * d < -n) return d + n;
-    return d;
-}
-
-// x_a - x_b from the per-step reference cells and FP32 offsets.
-__device__ __forceinline__ void disp(const AtomArgs &A, float4 pa, const int ca[3], float4 pb, float d[3]) {
-    int cb[3];
-    unpack_cref(pb.w, cb);
-    d[0] = (float)wrapdiff(ca[0] - cb[0], A.nc[0]) * A.h[0] + (pa.x - pb.x);
-    d[1] = (float)wrapdiff(ca[1] - cb[1], A.nc[1]) * A.h[1] + (pa.y - pb.y);
-    d[2] = (float)wrapdiff(ca[2] - cb[2], A.nc[2]) * A.h[2] + (pa.z - pb.z);
-}
-
 __device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
     s = a + b;
     const float bp = s - a;
     e = (a - (s - bp)) + (b - bp);
 }
 
-// x_a - x_b as an unevaluated pair dh + dl (error-free transformations).
-__device__ __forceinline__ void disp_df(const AtomArgs &A, float4 pa, float4 la, const int ca[3], float4 pb,
-                                        float4 lb, float dh[3], float dl[3]) {
-    int cb[3];
-    unpack_cref(pb.w, cb);
+// x_a - x_b, minimum image, as hi part dh (exact) and lo part dl. In the
+// step frame every coordinate hi sits inside one binade [B, 2B) with B >= 2L,
+// so hi_a - hi_b and the fold by a whole box length are exact; the lo parts
+// (below one ulp of hi) differ with an error far below FP32 resolution.
+__device__ __forceinline__ void pair_disp(const AtomArgs &A, float4 pa, float4 la, float4 pb, float4 lb, float dh[3],
+                                          float dl[3]) {
     const float ha[3] = {pa.x, pa.y, pa.z}, hb[3] = {pb.x, pb.y, pb.z};
-    const float la3[3] = {la.x, la.y, la.z}, lb3[3] = {lb.x, lb.y, lb.z};
+    const float l1[3] = {la.x, la.y, la.z}, l2[3] = {lb.x, lb.y, lb.z};
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
-        const float dc = (float)wrapdiff(ca[d] - cb[d], A.nc[d]);
-        float s, e, s2, e2;
-        two_sum(ha[d], -hb[d], s, e);
-        two_sum(dc * A.h[d], s, s2, e2);
-        dh[d] = s2;
-        dl[d] = (e + e2) + ((la3[d] - lb3[d]) + dc * A.h_lo[d]);
+        const float s = ha[d] - hb[d];
+        dh[d] = fmaf(-A.Lf[d], rintf(s * A.inv_Lf[d]), s);
+        dl[d] = l1[d] - l2[d];
     }
 }
 
-// Neighbour-list entry: the atom index in the low kNbBits bits and, above it,
-// the wrapped difference of the two atoms' reference cells (cref_a - cref_q)
-// per axis as a 4-bit signed value. Reference cells are fixed within a
-// coupled step and lists are rebuilt at its first force evaluation, so the
-// stored differences stay valid for the whole list lifetime.
-constexpr int kNbBits = 20;
-__device__ __forceinline__ unsigned pack_nb(int q, const int dc[3]) {
-    return (unsigned)q | (((unsigned)dc[0] & 15u) << kNbBits) | (((unsigned)dc[1] & 15u) << (kNbBits + 4)) |
-           (((unsigned)dc[2] & 15u) << (kNbBits + 8));
-}
-__device__ __forceinline__ int nb_atom(unsigned e) { return (int)(e & ((1u << kNbBits) - 1u)); }
-__device__ __forceinline__ float nb_dc(unsigned e, int axis) {
-    // Move the 4-bit field to the top, then sign-extend it with an arithmetic shift.
-    return (float)((int)(e << (32 - kNbBits - 4 * (axis + 1))) >> 28);
+// Cell of an atom from its step-frame position (hi + lo): floor of the
+// offset from the frame origin over the cell side, wrapped into the grid.
+__device__ __forceinline__ void cell_of(const AtomArgs &A, float4 p, float4 l, int c[3]) {
+    c[0] = wrapi((int)floorf(((p.x - A.off[0]) + l.x) * A.inv_h[0]), A.nc[0]);
+    c[1] = wrapi((int)floorf(((p.y - A.off[1]) + l.y) * A.inv_h[1]), A.nc[1]);
+    c[2] = wrapi((int)floorf(((p.z - A.off[2]) + l.z) * A.inv_h[2]), A.nc[2]);
 }
 
-// x_a - x_q for a Lennard-Jones pair from its list entry: one FP32 rounding
-// of (cell difference) h + (hi_a - hi_q) + (lo_a - lo_q), about 2^-23 of the
-// offsets, far below what FP32 inputs already fix (bonds, whose stretch
-// cancels, keep the compensated disp_df).
-__device__ __forceinline__ void disp_nb(const AtomArgs &A, float4 pa, float4 la, unsigned e, float4 pq, float4 lq,
-                                        float d[3]) {
-    const float dx = nb_dc(e, 0), dy = nb_dc(e, 1), dz = nb_dc(e, 2);
-    d[0] = fmaf(dx, A.h[0], pa.x - pq.x) + fmaf(dx, A.h_lo[0], la.x - lq.x);
-    d[1] = fmaf(dy, A.h[1], pa.y - pq.y) + fmaf(dy, A.h_lo[1], la.y - lq.y);
-    d[2] = fmaf(dz, A.h[2], pa.z - pq.z) + fmaf(dz, A.h_lo[2], la.z - lq.z);
+// Position of an atom within its cell (0 <= t < h up to rounding), for the
+// reach test of the neighbour cells.
+__device__ __forceinline__ void in_cell(const AtomArgs &A, float4 p, float4 l, float t[3]) {
+    const float v[3] = {(p.x - A.off[0]) + l.x, (p.y - A.off[1]) + l.y, (p.z - A.off[2]) + l.z};
+#pragma unroll
+    for (int d = 0; d < 3; ++d) t[d] = v[d] - floorf(v[d] * A.inv_h[d]) * A.h[d];
 }
 
 // Harmonic bond force factor -k (r - r0) / r with r - r0 evaluated as
 // (r^2 - r0^2) / (r + r0) from a compensated r^2, so the stretch keeps its
 // relative precision when r is close to r0.
-__device__ __forceinline__ float bond_factor(const float dh[3], const float dl[3], float k, float r0) {
+__device__ __forceinline__ float bond_factor(const float dh_in[3], const float dl_in[3], float k, float r0) {
+    // Renormalise hi + lo (two-sum: a component of hi may be smaller than its
+    // lo) so lo is below half an ulp of hi and r = sqrt(hi part of r^2) stays
+    // exact to FP32 rounding.
+    float dh[3], dl[3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) two_sum(dh_in[d], dl_in[d], dh[d], dl[d]);
     float p[3], pe[3];
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
@@ -133,17 +98,19 @@ __device__ __forceinline__ int bucket_of(const AtomArgs &A, const int c[3]) {
     return ((c[2] & A.fmask[2]) * A.fold[1] + (c[1] & A.fmask[1])) * A.fold[0] + (c[0] & A.fmask[0]);
 }
 
-// Current cell of an atom from its reference cell and FP32 offset.
-__device__ __forceinline__ void current_cell(const AtomArgs &A, float4 p, const int cr[3], int c[3]) {
-    c[0] = wrapi(cr[0] + (int)floorf(p.x * A.inv_h[0]), A.nc[0]);
-    c[1] = wrapi(cr[1] + (int)floorf(p.y * A.inv_h[1]), A.nc[1]);
-    c[2] = wrapi(cr[2] + (int)floorf(p.z * A.inv_h[2]), A.nc[2]);
-}
-
 __device__ __forceinline__ bool bonded(const AtomArgs &A, int a, int b) {
     for (int s = A.bstart[a]; s < A.bstart[a + 1]; ++s)
         if (A.bpart[s] == b) return true;
     return false;
+}
+
+// Exact FP64 cell coordinate floor((x * nc) / L) mod nc.
+__device__ __forceinline__ int exact_cell(double x, int nc, double L) {
+    const double s = __ddiv_rn(__dmul_rn(x, (double)nc), L);
+    const double fl = floor(s);
+    if (!(fabs(fl) < 4.0e15)) return 0;
+    long long c = (long long)fl % nc;
+    return (int)(c < 0 ? c + nc : c);
 }
 
 // Conservative force on atom a at the positions P (buckets of generation g3),
@@ -155,9 +122,10 @@ __device__ __forceinline__ bool bonded(const AtomArgs &A, int a, int b) {
 __device__ void md_force_warp(const AtomArgs &A, const float4 *__restrict__ P, const float4 *__restrict__ Lq, int g3,
                               int a, float4 pa, float4 la, float F[3]) {
     const int lane = threadIdx.x & 31;
-    int ca[3], cc[3];
-    unpack_cref(pa.w, ca);
-    current_cell(A, pa, ca, cc);
+    // The buckets hold exact FP64 cells here (set_state): search around the
+    // atom's own exact cell.
+    int cc[3];
+    for (int d = 0; d < 3; ++d) cc[d] = exact_cell(A.X[d * A.na + a], A.nc[d], A.Ld[d]);
     const int *__restrict__ cnt = A.count[g3];
     const int *__restrict__ slots = A.slot[g3];
     // Lane k < 27 owns neighbour cell k: its bucket and candidate count.
@@ -189,17 +157,9 @@ __device__ void md_force_warp(const AtomArgs &A, const float4 *__restrict__ P, c
         if (t >= total) continue;
         const int q = slots[(size_t)cb * A.cap + (t - before)];
         if (q == a) continue;
-        const float4 pq = P[q];
-        float d[3];
-        disp(A, pa, ca, pq, d);
-        if (!(d[0] * d[0] + d[1] * d[1] + d[2] * d[2] < A.rc2f * 1.0001f)) continue;
-        {
-            float dh[3], dl[3];
-            disp_df(A, pa, la, ca, pq, Lq[q], dh, dl);
-            d[0] = dh[0] + dl[0];
-            d[1] = dh[1] + dl[1];
-            d[2] = dh[2] + dl[2];
-        }
+        float dh[3], dl[3];
+        pair_disp(A, pa, la, P[q], Lq[q], dh, dl);
+        const float d[3] = {dh[0] + dl[0], dh[1] + dl[1], dh[2] + dl[2]};
         const float r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
         if (!(r2 < A.rc2f)) continue;
         if (bonded(A, a, q)) continue;
@@ -214,7 +174,7 @@ __device__ void md_force_warp(const AtomArgs &A, const float4 *__restrict__ P, c
     for (int s = A.bstart[a] + lane; s < A.bstart[a + 1]; s += 32) {
         const int q = A.bpart[s];
         float dh[3], dl[3];
-        disp_df(A, pa, la, ca, P[q], Lq[q], dh, dl);
+        pair_disp(A, pa, la, P[q], Lq[q], dh, dl);
         const float fr = bond_factor(dh, dl, A.bk[s], A.br0[s]);
         fx += fr * (dh[0] + dl[0]);
         fy += fr * (dh[1] + dl[1]);
@@ -330,39 +290,15 @@ __global__ void __launch_bounds__(128) k_sort_scatter(AtomArgs A) {
     if (pos >= 0 && pos < A.na) A.order[pos] = a;
 }
 
-// Exact FP64 cell coordinate floor((x * nc) / L) mod nc.
-__device__ __forceinline__ int exact_cell(double x, int nc, double L) {
-    const double s = __ddiv_rn(__dmul_rn(x, (double)nc), L);
-    const double fl = floor(s);
-    if (!(fabs(fl) < 4.0e15)) return 0;
-    long long c = (long long)fl % nc;
-    return (int)(c < 0 ? c + nc : c);
-}
 
-// set_state: reference frame at generation 0, exact binning, empty records.
+// set_state: step frame at generation 0, exact binning, empty records.
 __global__ void k_prime_insert(AtomArgs A) {
     const int a = blockIdx.x * blockDim.x + threadIdx.x;
     if (a >= A.na) return;
-    int cr[3];
-    float p0[3], r0[3];
-    bool finite = true;
-    for (int d = 0; d < 3; ++d) {
-        const double x = A.X[d * A.na + a];
-        finite = finite && isfinite(x);
-        const double s = x * ((double)A.nc[d] / A.Ld[d]);
-        double fl = floor(s);
-        if (!(fabs(fl) < 4.0e15)) fl = 0.0;
-        long long c = (long long)fl % A.nc[d];
-        cr[d] = (int)(c < 0 ? c + A.nc[d] : c);
-        const double off = (s - fl) * A.hd[d];
-        p0[d] = (float)off;
-        r0[d] = (float)(off - (double)p0[d]);
-        A.P0[d * A.na + a] = p0[d];
-        A.R0[d * A.na + a] = r0[d];
-    }
-    if (!finite) atomicOr(&A.ds->flags, FLAG_NONFINITE);
-    A.P[0][a] = make_float4(p0[0], p0[1], p0[2], pack_cref(cr));
-    A.L[0][a] = make_float4(r0[0], r0[1], r0[2], 0.f);
+    float4 p, l;
+    if (!set_frame(A, a, p, l)) atomicOr(&A.ds->flags, FLAG_NONFINITE);
+    A.P[0][a] = p;
+    A.L[0][a] = l;
     int c[3];
     for (int d = 0; d < 3; ++d) c[d] = exact_cell(A.X[d * A.na + a], A.nc[d], A.Ld[d]);
     insert(A, 0, a, c);
@@ -390,33 +326,33 @@ __global__ void k_prime_force(AtomArgs A) {
 // Builds atom a's list with the warp (27-cell search, ballot compaction).
 // Candidates are taken NBB per lane per round: all their slot loads are
 // issued together, then all their position loads, so a round costs two
-// dependent memory latencies. Bonded partners (the first 32) sit one per lane
-// and are matched with shuffles, without touching memory per candidate.
-template <int NBB, bool WRAP>
-__device__ __noinline__ void build_list(const AtomArgs &A, const float4 *__restrict__ P, int g3, int a, float4 pa, int b0,
-                           int b1) {
+// dependent memory latencies. Neighbour cells wholly beyond the list radius
+// are skipped; bonded partners (the first 32) sit one per lane and are
+// matched with shuffles, without touching memory per candidate.
+template <int NBB>
+__device__ __noinline__ void build_list(const AtomArgs &A, const float4 *__restrict__ P,
+                                        const float4 *__restrict__ Lq, int g3, int a, float4 pa, float4 la, int b0,
+                                        int b1) {
     const int lane = threadIdx.x & 31;
-    int ca[3], cc[3];
-    unpack_cref(pa.w, ca);
-    current_cell(A, pa, ca, cc);
+    int cc[3];
+    cell_of(A, pa, la, cc);
     const int nbond = b1 - b0;
     const int partner = lane < nbond ? A.bpart[b0 + lane] : -1;
     int bucket = 0, n = 0;
     if (lane < 27) {
         const int o[3] = {lane % 3 - 1, (lane / 3) % 3 - 1, lane / 9 - 1};
-        // Skip a neighbour cell that lies wholly beyond the list radius: the
-        // gap to it along each axis is the atom's distance to the shared face
-        // (t = position within its own cell). A small margin keeps the test
-        // conservative under rounding.
-        const float pv[3] = {pa.x, pa.y, pa.z};
+        // The gap to a neighbour cell along each axis is the atom's distance
+        // to the shared face; the margin keeps the test conservative under
+        // rounding.
+        float t[3];
+        in_cell(A, pa, la, t);
         float gap2 = 0.f;
 #pragma unroll
         for (int d = 0; d < 3; ++d) {
-            const float t = pv[d] - floorf(pv[d] * A.inv_h[d]) * A.h[d];
-            const float g = o[d] < 0 ? t : (o[d] > 0 ? A.h[d] - t : 0.f);
+            const float g = o[d] < 0 ? t[d] : (o[d] > 0 ? A.h[d] - t[d] : 0.f);
             gap2 += g * g;
         }
-        if (gap2 < A.rl2 * 1.0001f) {
+        if (gap2 < A.rl2 * 1.001f) {
             const int c[3] = {wrapi(cc[0] + o[0], A.nc[0]), wrapi(cc[1] + o[1], A.nc[1]),
                               wrapi(cc[2] + o[2], A.nc[2])};
             bucket = bucket_of(A, c);
@@ -447,40 +383,29 @@ __device__ __noinline__ void build_list(const AtomArgs &A, const float4 *__restr
             const int before = __shfl_sync(0xffffffffu, incl - n, pos & 31);
             q[u] = t < total ? A.slot[g3][(size_t)cb * A.cap + (t - before)] : -1;
         }
-        float4 pq[NBB];
+        float4 pq[NBB], lq[NBB];
 #pragma unroll
         for (int u = 0; u < NBB; ++u)
-            if (q[u] >= 0) pq[u] = P[q[u]];
+            if (q[u] >= 0) {
+                pq[u] = P[q[u]];
+                lq[u] = Lq[q[u]];
+            }
 #pragma unroll
         for (int u = 0; u < NBB; ++u) {
             bool keep = false;
-            int dc[3] = {0, 0, 0};
             if (q[u] >= 0 && q[u] != a) {
-                int cq[3];
-                unpack_cref(pq[u].w, cq);
-                const float pav[3] = {pa.x, pa.y, pa.z}, pqv[3] = {pq[u].x, pq[u].y, pq[u].z};
-                float r2 = 0.f;
-#pragma unroll
-                for (int d = 0; d < 3; ++d) {
-                    dc[d] = WRAP ? wrapdiff(ca[d] - cq[d], A.nc[d]) : ca[d] - cq[d];
-                    const float dd = fmaf((float)dc[d], A.h[d], pav[d] - pqv[d]);
-                    r2 += dd * dd;
-                }
-                keep = r2 < A.rl2;
+                float dh[3], dl[3];
+                pair_disp(A, pa, la, pq[u], lq[u], dh, dl);
+                const float d[3] = {dh[0] + dl[0], dh[1] + dl[1], dh[2] + dl[2]};
+                keep = d[0] * d[0] + d[1] * d[1] + d[2] * d[2] < A.rl2;
             }
             bool is_bonded = false;
             for (int l = 0; l < min(nbond, 32); ++l) is_bonded |= __shfl_sync(0xffffffffu, partner, l) == q[u];
             if (keep && nbond > 32 && !is_bonded) is_bonded = bonded(A, a, q[u]);
             keep = keep && !is_bonded;
-            // Reference cells of listed pairs are at most a few cells apart;
-            // a difference beyond the 4-bit field is reported, not stored.
-            if (keep && ((unsigned)(dc[0] + 8) | (unsigned)(dc[1] + 8) | (unsigned)(dc[2] + 8)) >= 16u) {
-                atomicOr(&A.ds->flags, FLAG_CELL);
-                keep = false;
-            }
             const unsigned m = __ballot_sync(0xffffffffu, keep);
             const int at = kept + __popc(m & ((1u << lane) - 1u));
-            if (keep && at < NL_MAX) out[at] = (int)pack_nb(q[u], dc);
+            if (keep && at < NL_MAX) out[at] = q[u];
             kept += __popc(m);
         }
     }
@@ -498,15 +423,6 @@ __device__ __noinline__ void build_list(const AtomArgs &A, const float4 *__restr
 // per-atom reductions.
 constexpr int NBB = 2;  // candidates per lane per round of a list build
 
-// A reference cell this far from every periodic boundary has no listed
-// neighbour across one (reference cells of listed pairs differ by at most a
-// few cells), so its list build can skip the minimum-image wrap.
-__device__ __forceinline__ bool near_boundary(const AtomArgs &A, const int c[3]) {
-    bool near = false;
-#pragma unroll
-    for (int d = 0; d < 3; ++d) near = near || c[d] < 8 || c[d] > A.nc[d] - 9;
-    return near;
-}
 
 // Conservative force on atom a from its list (nn entries) and its bonds
 // (slots b0..b1), over the TPA lanes of its group; every lane of the group
@@ -515,8 +431,6 @@ template <int TPA, int NB>
 __device__ __forceinline__ void list_force(const AtomArgs &A, const float4 *__restrict__ P,
                                            const float4 *__restrict__ Lq, int a, float4 pa, float4 la, int sub,
                                            int nn, int b0, int b1, float F[3]) {
-    int ca[3];
-    unpack_cref(pa.w, ca);
     // The first bond of each lane: its loads go out with the first round.
     const int sb = b0 + sub;
     int qb = -1;
@@ -527,27 +441,26 @@ __device__ __forceinline__ void list_force(const AtomArgs &A, const float4 *__re
         r0b = A.br0[sb];
     }
     float fx = 0.f, fy = 0.f, fz = 0.f;
-    const unsigned *__restrict__ lst = reinterpret_cast<const unsigned *>(A.nbr) + (size_t)a * NL_MAX;
+    const int *__restrict__ lst = A.nbr + (size_t)a * NL_MAX;
     for (int j0 = sub; j0 < nn; j0 += TPA * NB) {
-        unsigned e[NB];
+        int q[NB];
 #pragma unroll
         for (int u = 0; u < NB; ++u) {
             const int j = j0 + u * TPA;
-            e[u] = j < nn ? lst[j] : 0u;
+            q[u] = j < nn ? lst[j] : a;
         }
         float4 ph[NB], pl[NB];
 #pragma unroll
-        for (int u = 0; u < NB; ++u)
-            if (j0 + u * TPA < nn) {
-                const int q = nb_atom(e[u]);
-                ph[u] = P[q];
-                pl[u] = Lq[q];
-            }
+        for (int u = 0; u < NB; ++u) {
+            ph[u] = P[q[u]];
+            pl[u] = Lq[q[u]];
+        }
 #pragma unroll
         for (int u = 0; u < NB; ++u) {
             if (j0 + u * TPA >= nn) continue;
-            float d[3];
-            disp_nb(A, pa, la, e[u], ph[u], pl[u], d);
+            float dh[3], dl[3];
+            pair_disp(A, pa, la, ph[u], pl[u], dh, dl);
+            const float d[3] = {dh[0] + dl[0], dh[1] + dl[1], dh[2] + dl[2]};
             const float r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
             if (r2 < A.rc2f) {
                 const float inv_r2 = 1.0f / r2;
@@ -569,7 +482,7 @@ __device__ __forceinline__ void list_force(const AtomArgs &A, const float4 *__re
             r0 = A.br0[s];
         }
         float dh[3], dl[3];
-        disp_df(A, pa, la, ca, P[q], Lq[q], dh, dl);
+        pair_disp(A, pa, la, P[q], Lq[q], dh, dl);
         const float fr = bond_factor(dh, dl, k, r0);
         fx += fr * (dh[0] + dl[0]);
         fy += fr * (dh[1] + dl[1]);
@@ -602,27 +515,33 @@ __device__ __forceinline__ float4 shfl4(float4 v, int src) {
 // and lane 0 re-bins the atom.
 template <int TPA, int NB>
 __global__ void __launch_bounds__(128, TPA == 8 ? 9 : 8) k_md_substep(AtomArgs A, int k) {
-    // With programmatic dependent launch this kernel may start before the
-    // previous substep has finished: wait for its results first.
-    cudaGridDependencySynchronize();
     const int lane = threadIdx.x & 31;
     const int sub = lane & (TPA - 1);
     const int slot = ((blockIdx.x * blockDim.x + threadIdx.x) >> 5) * (32 / TPA) + lane / TPA;
     const int na = A.na;
+    // With programmatic dependent launch this kernel starts while the
+    // previous one (substep k-1, or the interpolation for k = 0) still runs.
+    // What neither of them writes is read before waiting on it: the step
+    // counter (advanced at the end of the previous coupled step), the atom
+    // order (sorted before the interpolation), masses and bond ranges.
     const int step = A.ds->step;
-    const int fl0 = A.ds->nl_flag[0], fl1 = A.ds->nl_flag[1], fl2 = A.ds->nl_flag[2];
     const int warp_first = slot - lane / TPA;
     const int a = warp_first < na ? A.order[slot < na ? slot : warp_first] : 0;
+    const float im = A.inv_m[a];
+    const int b0 = A.bstart[a], b1 = A.bstart[a + 1];
+    cudaGridDependencySynchronize();
+    // Let the next substep's blocks be scheduled as this grid's retire; they
+    // wait for this grid's completion in their own synchronisation above.
+    cudaTriggerProgrammaticLaunchCompletion();
+    const int fl0 = A.ds->nl_flag[0], fl1 = A.ds->nl_flag[1], fl2 = A.ds->nl_flag[2];
     const int g3 = ((step % 3) * (A.n_md % 3) + k) % 3;
     const int gn3 = (g3 + 1) % 3, gp3 = (g3 + 2) % 3;
     const int par = ((step & 1) * (A.n_md & 1) + k) & 1;
     const int rebuild = g3 == 0 ? fl0 : (g3 == 1 ? fl1 : fl2);
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         A.ds->nl_flag[gp3] = 0;
-        // Kernel 0 evaluates no force. The reference cells were reset for this
-        // coupled step, so kernel 1 rebuilds every list (their entries hold
-        // reference-cell differences).
-        if (k == 0) atomicOr(&A.ds->nl_flag[gn3], 1);
+        // Kernel 0 evaluates no force: hand a pending rebuild on to kernel 1.
+        if (k == 0 && rebuild) atomicOr(&A.ds->nl_flag[gn3], 1);
     }
     if (warp_first >= na) return;  // whole warp past the end
     const bool valid = slot < na;
@@ -632,11 +551,9 @@ __global__ void __launch_bounds__(128, TPA == 8 ? 9 : 8) k_md_substep(AtomArgs A
     const float vd = A.V[dcomp * na + a], Ud = A.U[dcomp * na + a];
     const float Jd = k == 0 ? 0.f : A.J[dcomp * na + a];
     const float Dold = A.D[dcomp * na + a];
-    const float im = A.inv_m[a];
     const float4 pa = A.P[par][a];
     const float4 la = A.L[par][a];
     const int nn = A.nnb[a];
-    const int b0 = A.bstart[a], b1 = A.bstart[a + 1];
     const int old_bucket = sub == 0 && k < A.n_md ? A.bucket[gp3][a] : 0;
     float F[3] = {0.f, 0.f, 0.f};
     if (k == 0) {
@@ -660,14 +577,8 @@ __global__ void __launch_bounds__(128, TPA == 8 ? 9 : 8) k_md_substep(AtomArgs A
                 const int vg = __shfl_sync(0xffffffffu, (int)valid, g * TPA);
                 const int bg0 = __shfl_sync(0xffffffffu, b0, g * TPA), bg1 = __shfl_sync(0xffffffffu, b1, g * TPA);
                 const float4 pg = shfl4(pa, g * TPA);
-                if (vg) {
-                    int cg[3];
-                    unpack_cref(pg.w, cg);
-                    if (near_boundary(A, cg))
-                        build_list<NBB, true>(A, A.P[par], g3, ag, pg, bg0, bg1);
-                    else
-                        build_list<NBB, false>(A, A.P[par], g3, ag, pg, bg0, bg1);
-                }
+                const float4 lg = shfl4(la, g * TPA);
+                if (vg) build_list<NBB>(A, A.P[par], A.L[par], g3, ag, pg, lg, bg0, bg1);
             }
             __syncwarp();
             nlist = A.nnb[a];
@@ -723,13 +634,12 @@ __global__ void __launch_bounds__(128, TPA == 8 ? 9 : 8) k_md_substep(AtomArgs A
     const float D2 = __shfl_sync(gm, Dd * Dd, base) + __shfl_sync(gm, Dd * Dd, base + 1) +
                      __shfl_sync(gm, Dd * Dd, base + 2);
     if (sub != 0) return;
-    const float4 pn = make_float4(px, py, pz, pa.w);
+    const float4 pn = make_float4(px, py, pz, 0.f), ln = make_float4(lx, ly, lz, 0.f);
     A.P[par ^ 1][a] = pn;
-    A.L[par ^ 1][a] = make_float4(lx, ly, lz, 0.f);
+    A.L[par ^ 1][a] = ln;
     A.count[gp3][old_bucket] = 0;
-    int cr[3], c[3];
-    unpack_cref(pa.w, cr);
-    current_cell(A, pn, cr, c);
+    int c[3];
+    cell_of(A, pn, ln, c);
     insert(A, gn3, a, c);
     if (!(isfinite(px) && isfinite(py) && isfinite(pz))) atomicOr(&A.ds->flags, FLAG_NONFINITE);
     // Drift since the last list build: past half the skin a pair may have
