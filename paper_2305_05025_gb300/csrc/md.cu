@@ -519,20 +519,18 @@ __global__ void __launch_bounds__(128, TPA == 8 ? 9 : 8) k_md_substep(AtomArgs A
     const int sub = lane & (TPA - 1);
     const int slot = ((blockIdx.x * blockDim.x + threadIdx.x) >> 5) * (32 / TPA) + lane / TPA;
     const int na = A.na;
-    // With programmatic dependent launch this kernel starts while the
-    // previous one (substep k-1, or the interpolation for k = 0) still runs.
-    // What neither of them writes is read before waiting on it: the step
-    // counter (advanced at the end of the previous coupled step), the atom
-    // order (sorted before the interpolation), masses and bond ranges.
+    // Launched with programmatic dependent launch: what the previous kernel
+    // (substep k-1, or the interpolation for k = 0) does not write is read
+    // before waiting on it: the step counter (advanced at the end of the
+    // previous coupled step), the atom order (sorted before the
+    // interpolation), masses and bond ranges. (An early trigger of the next
+    // substep's launch measured slower: its waiting blocks hold SM slots.)
     const int step = A.ds->step;
     const int warp_first = slot - lane / TPA;
     const int a = warp_first < na ? A.order[slot < na ? slot : warp_first] : 0;
     const float im = A.inv_m[a];
     const int b0 = A.bstart[a], b1 = A.bstart[a + 1];
     cudaGridDependencySynchronize();
-    // Let the next substep's blocks be scheduled as this grid's retire; they
-    // wait for this grid's completion in their own synchronisation above.
-    cudaTriggerProgrammaticLaunchCompletion();
     const int fl0 = A.ds->nl_flag[0], fl1 = A.ds->nl_flag[1], fl2 = A.ds->nl_flag[2];
     const int g3 = ((step % 3) * (A.n_md % 3) + k) % 3;
     const int gn3 = (g3 + 1) % 3, gp3 = (g3 + 2) % 3;
