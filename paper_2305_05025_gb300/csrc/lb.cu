@@ -137,7 +137,7 @@ __device__ __forceinline__ void pull_pair(const typename Store<S>::T *sp, ptrdif
 // neighbouring lane's word (or one 16-bit load at a row or warp edge), and
 // both results leave as one 32-bit store.
 template <int S, int FD>
-__global__ void __launch_bounds__(128, 8) k_lb_step_pair16(Lat L, typename Store<S>::T *b0, typename Store<S>::T *b1,
+__global__ void __launch_bounds__(128, 7) k_lb_step_pair16(Lat L, typename Store<S>::T *b0, typename Store<S>::T *b1,
                                                         DevState *ds) {
     using T = typename Store<S>::T;
     using H = Half16<S>;
@@ -172,21 +172,17 @@ __global__ void __launch_bounds__(128, 8) k_lb_step_pair16(Lat L, typename Store
     else
         pull_pair<S, false>(src + node, plane, oym, oyp, ozm, ozp, false, false, left_ok, right_ok, xl, xr, w);
     if (!active) return;
-    // Both nodes share g (the pair kernel runs only when g is uniform along x).
+    // Both nodes share g (the pair kernel runs only when g is uniform along x);
+    // their collisions run side by side in packed FP32x2 lanes.
     const float ga = body_amp(L, xx, yy, z);
-    float fa[Q], fb[Q];
+    float2 fab[Q];
 #pragma unroll
-    for (int i = 0; i < Q; ++i) {
-        const float2 v = H::unpack(w[i]);
-        fa[i] = v.x;
-        fb[i] = v.y;
-    }
-    const float ra = collide_g<FD, Store<S>::kScaled>(L, fa, ga);
-    const float rb = collide_g<FD, Store<S>::kScaled>(L, fb, ga);
-    if (!isfinite(ra) || !isfinite(rb)) atomicOr(&ds->flags, FLAG_NONFINITE);
+    for (int i = 0; i < Q; ++i) fab[i] = H::unpack(w[i]);
+    const float2 r = collide_g2<FD, Store<S>::kScaled>(L, fab, ga);
+    if (!isfinite(r.x) || !isfinite(r.y)) atomicOr(&ds->flags, FLAG_NONFINITE);
     T *dp = dst + node;
 #pragma unroll
-    for (int i = 0; i < Q; ++i, dp += plane) __stcs(reinterpret_cast<unsigned *>(dp), H::pack(fa[i], fb[i]));
+    for (int i = 0; i < Q; ++i, dp += plane) __stcs(reinterpret_cast<unsigned *>(dp), H::pack(fab[i].x, fab[i].y));
 }
 
 // Nodes touched by atoms: redo the collision with F = g + G from the same

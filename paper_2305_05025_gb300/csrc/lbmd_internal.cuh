@@ -269,6 +269,105 @@ __device__ __forceinline__ float collide_g(const Lat &L, float f[Q], float ga) {
     return rho;
 }
 
+// Packed FP32x2 arithmetic (two independent IEEE FP32 lanes per instruction).
+__device__ __forceinline__ float2 f2(float a) { return make_float2(a, a); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __ffma2_rn(b, f2(-1.f), a); }  // a - b, one rounding
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 neg2(float2 a) { return make_float2(-a.x, -a.y); }
+
+// collide_g for two nodes at once that share the body force (the node pairs
+// of the 16-bit kernel): the same operations, each on a pair of FP32 lanes
+// with the packed FP32x2 instructions, so every lane rounds exactly as one
+// scalar operation would. Returns both densities.
+template <int FD, bool SCALED>
+__device__ __forceinline__ float2 collide_g2(const Lat &L, float2 f[Q], float ga) {
+    constexpr float sc = SCALED ? kF16Scale : 1.f, isc = SCALED ? kF16Unscale : 1.f;
+    float2 sp[9], dp[9];
+#pragma unroll
+    for (int p = 0; p < 9; ++p) {
+        sp[p] = add2(f[2 * p + 1], f[2 * p + 2]);
+        dp[p] = sub2(f[2 * p + 1], f[2 * p + 2]);
+    }
+    float2 drho = f[0], jx = f2(0.f), jy = f2(0.f), jz = f2(0.f);
+#pragma unroll
+    for (int p = 0; p < 9; ++p) {
+        drho = add2(drho, sp[p]);
+        if (cx(2 * p + 1)) jx = cx(2 * p + 1) > 0 ? add2(jx, dp[p]) : sub2(jx, dp[p]);
+        if (cy(2 * p + 1)) jy = cy(2 * p + 1) > 0 ? add2(jy, dp[p]) : sub2(jy, dp[p]);
+        if (cz(2 * p + 1)) jz = cz(2 * p + 1) > 0 ? add2(jz, dp[p]) : sub2(jz, dp[p]);
+    }
+    if (SCALED) {
+        drho = mul2(drho, f2(isc));
+        jx = mul2(jx, f2(isc));
+        jy = mul2(jy, f2(isc));
+        jz = mul2(jz, f2(isc));
+    }
+    const float2 rho = add2(f2(L.rho0), drho);
+    const float2 inv = make_float2(1.f / rho.x, 1.f / rho.y);
+    if (FD == 0) jx = add2(jx, f2(0.5f * ga));
+    if (FD == 1) jy = add2(jy, f2(0.5f * ga));
+    if (FD == 2) jz = add2(jz, f2(0.5f * ga));
+    const float2 ux = mul2(jx, inv), uy = mul2(jy, inv), uz = mul2(jz, inv);
+    const float2 usq = fma2(uz, uz, fma2(uy, uy, mul2(ux, ux)));
+    const float om = L.omega, s = 1.f - 0.5f * om, keep = 1.f - om;
+    float2 A0 = mul2(f2(om), fma2(mul2(f2(-1.5f), rho), usq, drho));
+    if (FD >= 0) {
+        const float2 uF = mul2(FD == 0 ? ux : (FD == 1 ? uy : uz), f2(ga));
+        A0 = fma2(f2(-3.f * s), uF, A0);
+    }
+    const float2 orho = mul2(f2(om), rho);
+    constexpr float wf = sc / 18.f, we = sc / 36.f;
+    const float2 A0f = mul2(f2(wf), A0), A0e = mul2(f2(we), A0);
+    const float2 k45f = mul2(f2(4.5f * wf), orho), k45e = mul2(f2(4.5f * we), orho);
+    const float2 k3f = mul2(f2(3.f * wf), orho), k3e = mul2(f2(3.f * we), orho);
+    const float sga = s * ga;
+    const float2 a9f = f2((9.f * wf) * sga), a9e = f2((9.f * we) * sga);
+    const float2 a3f = f2((3.f * wf) * sga), a3e = f2((3.f * we) * sga);
+    const float2 Ppf = add2(a9f, k3f), Pmf = sub2(a9f, k3f), Qpf = add2(A0f, a3f), Qmf = sub2(A0f, a3f);
+    const float2 Ppe = add2(a9e, k3e), Pme = sub2(a9e, k3e), Qpe = add2(A0e, a3e), Qme = sub2(A0e, a3e);
+    f[0] = fma2(f2(keep), f[0], mul2(f2(sc / 3.f), A0));
+#pragma unroll
+    for (int i = 1; i < Q; i += 2) {
+        const bool face = i <= 6;
+        float2 cu = f2(0.f);
+        bool first = true;
+        if (cx(i)) {
+            cu = cx(i) > 0 ? ux : neg2(ux);
+            first = false;
+        }
+        if (cy(i)) {
+            cu = first ? (cy(i) > 0 ? uy : neg2(uy)) : (cy(i) > 0 ? add2(cu, uy) : sub2(cu, uy));
+            first = false;
+        }
+        if (cz(i)) cu = first ? (cz(i) > 0 ? uz : neg2(uz)) : (cz(i) > 0 ? add2(cu, uz) : sub2(cu, uz));
+        const int cf = FD == 0 ? cx(i) : (FD == 1 ? cy(i) : (FD == 2 ? cz(i) : 0));
+        const float2 k45 = face ? k45f : k45e;
+        float2 inP, inM, outP, outM;  // E + O = fma(cu, fma(k45, cu, inP), outP), E - O with inM, outM
+        if (cf == 0) {
+            inP = face ? k3f : k3e;
+            inM = neg2(inP);
+            outP = outM = face ? A0f : A0e;
+        } else if (cf > 0) {
+            inP = face ? Ppf : Ppe;
+            inM = face ? Pmf : Pme;
+            outP = face ? Qpf : Qpe;
+            outM = face ? Qmf : Qme;
+        } else {
+            inP = neg2(face ? Pmf : Pme);
+            inM = neg2(face ? Ppf : Ppe);
+            outP = face ? Qmf : Qme;
+            outM = face ? Qpf : Qpe;
+        }
+        const float2 EpO = fma2(cu, fma2(k45, cu, inP), outP);
+        const float2 EmO = fma2(cu, fma2(k45, cu, inM), outM);
+        f[i] = fma2(f2(keep), f[i], EpO);
+        f[i + 1] = fma2(f2(keep), f[i + 1], EmO);
+    }
+    return rho;
+}
+
 // Velocity u = (sum f c + g/2)/rho of a node from its pulled deviations.
 __device__ __forceinline__ float node_velocity(const Lat &L, const float f[Q], const float g[3], float u[3]) {
     float drho = 0.f, jx = 0.f, jy = 0.f, jz = 0.f;
