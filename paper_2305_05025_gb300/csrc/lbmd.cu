@@ -30,6 +30,9 @@ constexpr int kFold = 128;  // bucket grid per axis (cells folded modulo this)
 // atoms into a cell of side 1.3, and folding (cells 128 apart share a bucket
 // once a lattice axis holds more than 128 cells) can stack two globules.
 constexpr int kCap = 128;
+// Atoms per MD bucket on the half-size grid (a cell of side >= 0.65 holds
+// ~5 atoms of a collapsed globule; one fold can stack two regions).
+constexpr int kCapFine = 48;
 
 }  // namespace
 
@@ -222,6 +225,19 @@ void fill_physics(lbmd_t h) {
         A.off[d] = (float)A.offd[d];
     }
     A.cap = kCap;
+    // Half-size cells while each axis folds at most twice (a bucket then
+    // stacks cells 128 apart at most once); coarse cells on larger boxes.
+    bool fine = true;
+    for (int d = 0; d < 3; ++d) fine = fine && std::floor((double)Ls[d] / (0.5 * (rc + p.skin))) <= 2 * kFold;
+    A.bwin = fine ? 5 : 3;
+    for (int d = 0; d < 3; ++d) {
+        A.bnc[d] = h->na == 0 ? 6 : fine ? (int)std::floor((double)Ls[d] / (0.5 * (rc + p.skin))) : A.nc[d];
+        A.bfold[d] = A.bnc[d] < kFold ? A.bnc[d] : kFold;
+        A.bfmask[d] = A.bnc[d] <= kFold ? -1 : kFold - 1;
+        A.bh[d] = (float)((double)Ls[d] / A.bnc[d]);
+        A.binv_h[d] = (float)(A.bnc[d] / (double)Ls[d]);
+    }
+    A.bcap = fine ? kCapFine : kCap;
     h->C.L = L;
     h->C.na = h->na;
 }
@@ -406,7 +422,7 @@ lbmd_status adj_restore(lbmd_t h, int i, bool ck) {
     CK(h, cudaMemsetAsync(h->C.G, 0, N * sizeof(float4), s));
     CK(h, cudaMemcpyAsync(h->A.X, (ck ? h->ck_X : h->seg_X) + na3 * i, na3 * sizeof(double), cudaMemcpyDeviceToDevice, s));
     CK(h, cudaMemcpyAsync(h->A.V, (ck ? h->ck_V : h->seg_V) + na3 * i, na3 * sizeof(float), cudaMemcpyDeviceToDevice, s));
-    const size_t B = (size_t)h->A.fold[0] * h->A.fold[1] * h->A.fold[2];
+    const size_t B = (size_t)h->A.bfold[0] * h->A.bfold[1] * h->A.bfold[2];
     for (int g = 0; g < 3; ++g) {
         CK(h, cudaMemsetAsync(h->A.count[g], 0, B * sizeof(int), s));
         CK(h, cudaMemsetAsync(h->A.bucket[g], 0, na * sizeof(int), s));
@@ -541,10 +557,10 @@ lbmd_status lbmd_create(const lbmd_params *params, int n_atoms, const double *ma
         CREATE_TRY(dalloc_t(h, &C.frac, na3));
         C.touched_cap = 8 * na;
         CREATE_TRY(dalloc_t(h, &C.touched, (size_t)C.touched_cap));
-        const size_t B = (size_t)A.fold[0] * A.fold[1] * A.fold[2];
+        const size_t B = (size_t)A.bfold[0] * A.bfold[1] * A.bfold[2];
         for (int g = 0; g < 3; ++g) {
             CREATE_TRY(dalloc_t(h, &A.count[g], B));
-            CREATE_TRY(dalloc_t(h, &A.slot[g], B * A.cap));
+            CREATE_TRY(dalloc_t(h, &A.slot[g], B * A.bcap));
             CREATE_TRY(dalloc_t(h, &A.bucket[g], (size_t)na));
             CREATE_TRY(dalloc_t(h, &A.sidx[g], (size_t)na));
         }
@@ -648,7 +664,7 @@ lbmd_status lbmd_set_state(lbmd_t h, const float *f, const float *rho, const flo
         const size_t na3 = (size_t)3 * h->na;
         TRY(to_device(h, h->A.X, x, na3 * sizeof(double), on_device));
         TRY(to_device(h, h->A.V, v, na3 * sizeof(float), on_device));
-        const size_t B = (size_t)h->A.fold[0] * h->A.fold[1] * h->A.fold[2];
+        const size_t B = (size_t)h->A.bfold[0] * h->A.bfold[1] * h->A.bfold[2];
         for (int g = 0; g < 3; ++g) {
             CK(h, cudaMemsetAsync(h->A.count[g], 0, B * sizeof(int), h->stream));
             CK(h, cudaMemsetAsync(h->A.bucket[g], 0, h->na * sizeof(int), h->stream));

@@ -409,10 +409,19 @@ struct AtomArgs {
     float gamma;
     float lj_sig2, lj_24eps, lj_fc, rc2f;  // LJ constants; lj_fc = F_LJ(rc)
     double rc2d;          // rc^2 in FP64 (neighbour counts)
-    int nc[3];            // cell grid (side h = L/nc >= rc + skin)
+    int nc[3];            // cell grid (side h = L/nc >= rc + skin): the reported cell
+                          // list and the adjoint's buckets
     int fold[3];          // bucket grid: cell c -> bucket c mod fold
     int cap;              // slots per bucket
     float h[3], inv_h[3];
+    // Grid of the MD buckets (substeps, list builds, sort). While each axis
+    // folds at most twice at half the coarse side, cells of side
+    // bh = L/bnc >= (rc + skin)/2 searched as a 5x5x5 block (bwin = 5:
+    // about half the candidates of 27 coarse cells); on larger boxes the
+    // coarse cells searched as 3x3x3 (bwin = 3), since finer buckets folded
+    // many times over would stack far-apart atoms.
+    int bnc[3], bfold[3], bfmask[3], bcap, bwin;
+    float bh[3], binv_h[3];
     double hd[3], Ld[3];
     float Lf[3], inv_Lf[3];  // box lengths and their inverses
     float off[3];         // step-frame origin per axis (exact in FP32)

@@ -52,9 +52,9 @@ __device__ __forceinline__ void pair_disp(const AtomArgs &A, float4 pa, float4 l
 // Cell of an atom from its step-frame position (hi + lo): floor of the
 // offset from the frame origin over the cell side, wrapped into the grid.
 __device__ __forceinline__ void cell_of(const AtomArgs &A, float4 p, float4 l, int c[3]) {
-    c[0] = wrapi((int)floorf(((p.x - A.off[0]) + l.x) * A.inv_h[0]), A.nc[0]);
-    c[1] = wrapi((int)floorf(((p.y - A.off[1]) + l.y) * A.inv_h[1]), A.nc[1]);
-    c[2] = wrapi((int)floorf(((p.z - A.off[2]) + l.z) * A.inv_h[2]), A.nc[2]);
+    c[0] = wrapi((int)floorf(((p.x - A.off[0]) + l.x) * A.binv_h[0]), A.bnc[0]);
+    c[1] = wrapi((int)floorf(((p.y - A.off[1]) + l.y) * A.binv_h[1]), A.bnc[1]);
+    c[2] = wrapi((int)floorf(((p.z - A.off[2]) + l.z) * A.binv_h[2]), A.bnc[2]);
 }
 
 // Position of an atom within its cell (0 <= t < h up to rounding), for the
@@ -62,7 +62,7 @@ __device__ __forceinline__ void cell_of(const AtomArgs &A, float4 p, float4 l, i
 __device__ __forceinline__ void in_cell(const AtomArgs &A, float4 p, float4 l, float t[3]) {
     const float v[3] = {(p.x - A.off[0]) + l.x, (p.y - A.off[1]) + l.y, (p.z - A.off[2]) + l.z};
 #pragma unroll
-    for (int d = 0; d < 3; ++d) t[d] = v[d] - floorf(v[d] * A.inv_h[d]) * A.h[d];
+    for (int d = 0; d < 3; ++d) t[d] = v[d] - floorf(v[d] * A.binv_h[d]) * A.bh[d];
 }
 
 // Harmonic bond force factor -k (r - r0) / r with r - r0 evaluated as
@@ -95,7 +95,7 @@ __device__ __forceinline__ float bond_factor(const float dh_in[3], const float d
 // Bucket of a cell: cells fold onto a grid of at most 128 per axis (fold = nc
 // when nc <= 128, otherwise 128 and fmask = 127).
 __device__ __forceinline__ int bucket_of(const AtomArgs &A, const int c[3]) {
-    return ((c[2] & A.fmask[2]) * A.fold[1] + (c[1] & A.fmask[1])) * A.fold[0] + (c[0] & A.fmask[0]);
+    return ((c[2] & A.bfmask[2]) * A.bfold[1] + (c[1] & A.bfmask[1])) * A.bfold[0] + (c[0] & A.bfmask[0]);
 }
 
 __device__ __forceinline__ bool bonded(const AtomArgs &A, int a, int b) {
@@ -113,49 +113,90 @@ __device__ __forceinline__ int exact_cell(double x, int nc, double L) {
     return (int)(c < 0 ? c + nc : c);
 }
 
-// Conservative force on atom a at the positions P (buckets of generation g3),
-// evaluated by a whole warp: the candidates of the 27 neighbour cells are
-// numbered through a warp prefix sum over the cell counts and dealt round-robin
-// to the lanes (so every lane has about the same number of dependent loads in
-// flight), bonds are dealt the same way, and the three force components are
-// summed across the warp. Every lane returns the full force.
+// Candidate table of the W x W x W MD cells around cell cc (W = A.bwin, 3
+// or 5), for one warp. A cell wholly beyond `reach` of the atom (t: its
+// offset within cc; the gap along an axis is the distance to the near face
+// of that cell) counts zero. tab[k], k < 128: candidates in cells 0..k
+// (inclusive prefix, cells k >= W^3 empty); tab[128 + k]: bucket of cell k.
+// Returns the total.
+template <int W>
+__device__ __forceinline__ int cell_table(const AtomArgs &A, int g3, const int cc[3], const float t[3], float reach2,
+                                          int *tab) {
+    const int lane = threadIdx.x & 31;
+    constexpr int half = W / 2, ncell = W * W * W, rounds = (ncell + 31) / 32;
+    int run = 0;
+#pragma unroll
+    for (int m = 0; m < rounds; ++m) {
+        const int k = lane + 32 * m;
+        int n = 0, b = 0;
+        if (k < ncell) {
+            const int o[3] = {k % W - half, (k / W) % W - half, k / (W * W) - half};
+            float gap2 = 0.f;
+#pragma unroll
+            for (int d = 0; d < 3; ++d) {
+                const float g = o[d] < 0   ? t[d] + (float)(-o[d] - 1) * A.bh[d]
+                                : o[d] > 0 ? (A.bh[d] - t[d]) + (float)(o[d] - 1) * A.bh[d]
+                                           : 0.f;
+                gap2 += g * g;
+            }
+            if (gap2 < reach2 * 1.001f) {
+                const int c[3] = {wrapi(cc[0] + o[0], A.bnc[0]), wrapi(cc[1] + o[1], A.bnc[1]),
+                                  wrapi(cc[2] + o[2], A.bnc[2])};
+                b = bucket_of(A, c);
+                n = min(A.count[g3][b], A.bcap);
+            }
+        }
+        int incl = n;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int v = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += v;
+        }
+        tab[k] = run + incl;
+        tab[128 + k] = b;
+        run += __shfl_sync(0xffffffffu, incl, 31);
+    }
+#pragma unroll
+    for (int k = 32 * rounds + lane; k < 128; k += 32) tab[k] = run;  // empty cells past the block
+    __syncwarp();
+    return run;
+}
+
+// Table cell holding candidate t (the first cell whose inclusive count
+// exceeds t); `before` receives the candidates of the cells ahead of it.
+__device__ __forceinline__ int cand_cell(const int *tab, int t, int &before) {
+    int pos = 0;
+#pragma unroll
+    for (int step = 64; step > 0; step >>= 1)
+        if (tab[pos + step - 1] <= t) pos += step;
+    before = pos ? tab[pos - 1] : 0;
+    return pos;
+}
+
+// Conservative force on atom a at the positions P, from the buckets of
+// generation g3 that set_state fills with exact FP64 cells: a whole warp
+// walks the candidates of the MD cells within rc around the atom's own exact
+// cell (cell_table), bonds are dealt to the lanes, and the three components
+// are summed across the warp. Every lane returns the full force.
 __device__ void md_force_warp(const AtomArgs &A, const float4 *__restrict__ P, const float4 *__restrict__ Lq, int g3,
                               int a, float4 pa, float4 la, float F[3]) {
+    __shared__ int s_tab[4][256];
+    int *tab = s_tab[threadIdx.x >> 5];
     const int lane = threadIdx.x & 31;
-    // The buckets hold exact FP64 cells here (set_state): search around the
-    // atom's own exact cell.
     int cc[3];
-    for (int d = 0; d < 3; ++d) cc[d] = exact_cell(A.X[d * A.na + a], A.nc[d], A.Ld[d]);
-    const int *__restrict__ cnt = A.count[g3];
-    const int *__restrict__ slots = A.slot[g3];
-    // Lane k < 27 owns neighbour cell k: its bucket and candidate count.
-    int bucket = 0, n = 0;
-    if (lane < 27) {
-        const int ox = lane % 3 - 1, oy = (lane / 3) % 3 - 1, oz = lane / 9 - 1;
-        const int c[3] = {wrapi(cc[0] + ox, A.nc[0]), wrapi(cc[1] + oy, A.nc[1]), wrapi(cc[2] + oz, A.nc[2])};
-        bucket = bucket_of(A, c);
-        n = min(cnt[bucket], A.cap);
+    float t[3];
+    for (int d = 0; d < 3; ++d) {
+        const double x = A.X[d * A.na + a];
+        cc[d] = exact_cell(x, A.bnc[d], A.Ld[d]);
+        const double sx = x * ((double)A.bnc[d] / A.Ld[d]);
+        t[d] = (float)((sx - floor(sx)) * ((double)A.Ld[d] / A.bnc[d]));
     }
-    int incl = n;  // inclusive prefix sum over lanes
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const int t = __shfl_up_sync(0xffffffffu, incl, o);
-        if (lane >= o) incl += t;
-    }
-    const int total = __shfl_sync(0xffffffffu, incl, 31);
+    const int total = A.bwin == 5 ? cell_table<5>(A, g3, cc, t, A.rc2f, tab) : cell_table<3>(A, g3, cc, t, A.rc2f, tab);
     float fx = 0.f, fy = 0.f, fz = 0.f;
-    for (int t = lane; t - lane < total; t += 32) {
-        // Cell holding candidate t: first lane whose inclusive sum exceeds t.
-        int pos = 0;
-#pragma unroll
-        for (int step = 16; step > 0; step >>= 1) {
-            const int probe = __shfl_sync(0xffffffffu, incl, pos + step - 1);
-            if (probe <= t) pos += step;
-        }
-        const int cb = __shfl_sync(0xffffffffu, bucket, pos & 31);
-        const int before = __shfl_sync(0xffffffffu, incl - n, pos & 31);
-        if (t >= total) continue;
-        const int q = slots[(size_t)cb * A.cap + (t - before)];
+    for (int t0 = lane; t0 < total; t0 += 32) {
+        int before;
+        const int pos = cand_cell(tab, t0, before);
+        const int q = A.slot[g3][(size_t)tab[128 + pos] * A.bcap + (t0 - before)];
         if (q == a) continue;
         float dh[3], dl[3];
         pair_disp(A, pa, la, P[q], Lq[q], dh, dl);
@@ -171,11 +212,11 @@ __device__ void md_force_warp(const AtomArgs &A, const float4 *__restrict__ P, c
         fy += fr * d[1];
         fz += fr * d[2];
     }
-    for (int s = A.bstart[a] + lane; s < A.bstart[a + 1]; s += 32) {
-        const int q = A.bpart[s];
+    for (int sb = A.bstart[a] + lane; sb < A.bstart[a + 1]; sb += 32) {
+        const int q = A.bpart[sb];
         float dh[3], dl[3];
         pair_disp(A, pa, la, P[q], Lq[q], dh, dl);
-        const float fr = bond_factor(dh, dl, A.bk[s], A.br0[s]);
+        const float fr = bond_factor(dh, dl, A.bk[sb], A.br0[sb]);
         fx += fr * (dh[0] + dl[0]);
         fy += fr * (dh[1] + dl[1]);
         fz += fr * (dh[2] + dl[2]);
@@ -186,6 +227,7 @@ __device__ void md_force_warp(const AtomArgs &A, const float4 *__restrict__ P, c
         fy += __shfl_xor_sync(0xffffffffu, fy, o);
         fz += __shfl_xor_sync(0xffffffffu, fz, o);
     }
+    __syncwarp();
     F[0] = fx;
     F[1] = fy;
     F[2] = fz;
@@ -194,8 +236,8 @@ __device__ void md_force_warp(const AtomArgs &A, const float4 *__restrict__ P, c
 __device__ __forceinline__ void insert(const AtomArgs &A, int g3, int a, const int c[3]) {
     const int b = bucket_of(A, c);
     const int s = atomicAdd(&A.count[g3][b], 1);
-    if (s < A.cap)
-        A.slot[g3][(size_t)b * A.cap + s] = a;
+    if (s < A.bcap)
+        A.slot[g3][(size_t)b * A.bcap + s] = a;
     else
         atomicOr(&A.ds->flags, FLAG_CELL);
     A.bucket[g3][a] = b;
@@ -231,7 +273,7 @@ __global__ void __launch_bounds__(1024) k_sort_local(AtomArgs A) {
     const unsigned m = blockIdx.x * 1024u + threadIdx.x;
     const int x = compact3(m), y = compact3(m >> 1), z = compact3(m >> 2);
     int cnt = 0;
-    if (x < A.fold[0] && y < A.fold[1] && z < A.fold[2]) cnt = A.count[g3][(z * A.fold[1] + y) * A.fold[0] + x];
+    if (x < A.bfold[0] && y < A.bfold[1] && z < A.bfold[2]) cnt = A.count[g3][(z * A.bfold[1] + y) * A.bfold[0] + x];
     __shared__ int wsum[32];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     int incl = cnt;
@@ -284,7 +326,7 @@ __global__ void __launch_bounds__(128) k_sort_scatter(AtomArgs A) {
     const int step = A.ds->step;
     const int g3 = ((step % 3) * (A.n_md % 3)) % 3;
     const int b = A.bucket[g3][a];
-    const int x = b % A.fold[0], y = (b / A.fold[0]) % A.fold[1], z = b / (A.fold[0] * A.fold[1]);
+    const int x = b % A.bfold[0], y = (b / A.bfold[0]) % A.bfold[1], z = b / (A.bfold[0] * A.bfold[1]);
     const unsigned m = morton3(x, y, z);
     const int pos = A.scan_block[m >> 10] + A.scan_local[m] + A.sidx[g3][a];
     if (pos >= 0 && pos < A.na) A.order[pos] = a;
@@ -300,7 +342,7 @@ __global__ void k_prime_insert(AtomArgs A) {
     A.P[0][a] = p;
     A.L[0][a] = l;
     int c[3];
-    for (int d = 0; d < 3; ++d) c[d] = exact_cell(A.X[d * A.na + a], A.nc[d], A.Ld[d]);
+    for (int d = 0; d < 3; ++d) c[d] = exact_cell(A.X[d * A.na + a], A.bnc[d], A.Ld[d]);
     insert(A, 0, a, c);
     A.bucket[2][a] = 0;
     A.bucket[1][a] = 0;
@@ -323,65 +365,36 @@ __global__ void k_prime_force(AtomArgs A) {
 // the buckets of that generation, inside the same kernel. Flags rotate over
 // three slots like the buckets: kernel k reads slot g, raises g+1, clears g-1.
 
-// Builds atom a's list with the warp (27-cell search, ballot compaction).
-// Candidates are taken NBB per lane per round: all their slot loads are
-// issued together, then all their position loads, so a round costs two
-// dependent memory latencies. Neighbour cells wholly beyond the list radius
-// are skipped; bonded partners (the first 32) sit one per lane and are
-// matched with shuffles, without touching memory per candidate.
-template <int NBB>
+// Builds atom a's list with the warp: candidates of the MD cells within the
+// list radius (cell_table), NBB per lane per round (all
+// their slot loads issued together, then all their position loads, so a
+// round costs two dependent memory latencies), ballot compaction. Bonded
+// partners (the first 32) sit one per lane and are matched with shuffles,
+// without touching memory per candidate.
+template <int NBB, int W>
 __device__ __noinline__ void build_list(const AtomArgs &A, const float4 *__restrict__ P,
                                         const float4 *__restrict__ Lq, int g3, int a, float4 pa, float4 la, int b0,
                                         int b1) {
+    __shared__ int s_tab[4][256];
+    int *tab = s_tab[threadIdx.x >> 5];
     const int lane = threadIdx.x & 31;
     int cc[3];
     cell_of(A, pa, la, cc);
+    float t[3];
+    in_cell(A, pa, la, t);
     const int nbond = b1 - b0;
     const int partner = lane < nbond ? A.bpart[b0 + lane] : -1;
-    int bucket = 0, n = 0;
-    if (lane < 27) {
-        const int o[3] = {lane % 3 - 1, (lane / 3) % 3 - 1, lane / 9 - 1};
-        // The gap to a neighbour cell along each axis is the atom's distance
-        // to the shared face; the margin keeps the test conservative under
-        // rounding.
-        float t[3];
-        in_cell(A, pa, la, t);
-        float gap2 = 0.f;
-#pragma unroll
-        for (int d = 0; d < 3; ++d) {
-            const float g = o[d] < 0 ? t[d] : (o[d] > 0 ? A.h[d] - t[d] : 0.f);
-            gap2 += g * g;
-        }
-        if (gap2 < A.rl2 * 1.001f) {
-            const int c[3] = {wrapi(cc[0] + o[0], A.nc[0]), wrapi(cc[1] + o[1], A.nc[1]),
-                              wrapi(cc[2] + o[2], A.nc[2])};
-            bucket = bucket_of(A, c);
-            n = min(A.count[g3][bucket], A.cap);
-        }
-    }
-    int incl = n;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const int t = __shfl_up_sync(0xffffffffu, incl, o);
-        if (lane >= o) incl += t;
-    }
-    const int total = __shfl_sync(0xffffffffu, incl, 31);
+    const int total = cell_table<W>(A, g3, cc, t, A.rl2, tab);
     int kept = 0;
     int *__restrict__ out = A.nbr + (size_t)a * NL_MAX;
     for (int t0 = 0; t0 < total; t0 += 32 * NBB) {
         int q[NBB];
 #pragma unroll
         for (int u = 0; u < NBB; ++u) {
-            const int t = t0 + 32 * u + lane;
-            int pos = 0;  // cell holding candidate t: first lane whose inclusive sum exceeds t
-#pragma unroll
-            for (int step = 16; step > 0; step >>= 1) {
-                const int probe = __shfl_sync(0xffffffffu, incl, pos + step - 1);
-                if (probe <= t) pos += step;
-            }
-            const int cb = __shfl_sync(0xffffffffu, bucket, pos & 31);
-            const int before = __shfl_sync(0xffffffffu, incl - n, pos & 31);
-            q[u] = t < total ? A.slot[g3][(size_t)cb * A.cap + (t - before)] : -1;
+            const int tc = t0 + 32 * u + lane;
+            int before;
+            const int pos = cand_cell(tab, tc < total ? tc : total - 1, before);
+            q[u] = tc < total ? A.slot[g3][(size_t)tab[128 + pos] * A.bcap + (tc - before)] : -1;
         }
         float4 pq[NBB], lq[NBB];
 #pragma unroll
@@ -513,7 +526,7 @@ __device__ __forceinline__ float4 shfl4(float4 v, int src) {
 // the other (all 32 lanes on each); then each group evaluates its atom's
 // force over the list, lanes 0-2 of the group integrate one component each,
 // and lane 0 re-bins the atom.
-template <int TPA, int NB>
+template <int TPA, int NB, int W>
 __global__ void __launch_bounds__(128, TPA == 8 ? 9 : 8) k_md_substep(AtomArgs A, int k) {
     const int lane = threadIdx.x & 31;
     const int sub = lane & (TPA - 1);
@@ -576,7 +589,7 @@ __global__ void __launch_bounds__(128, TPA == 8 ? 9 : 8) k_md_substep(AtomArgs A
                 const int bg0 = __shfl_sync(0xffffffffu, b0, g * TPA), bg1 = __shfl_sync(0xffffffffu, b1, g * TPA);
                 const float4 pg = shfl4(pa, g * TPA);
                 const float4 lg = shfl4(la, g * TPA);
-                if (vg) build_list<NBB>(A, A.P[par], A.L[par], g3, ag, pg, lg, bg0, bg1);
+                if (vg) build_list<NBB, W>(A, A.P[par], A.L[par], g3, ag, pg, lg, bg0, bg1);
             }
             __syncwarp();
             nlist = A.nnb[a];
@@ -645,49 +658,58 @@ __global__ void __launch_bounds__(128, TPA == 8 ? 9 : 8) k_md_substep(AtomArgs A
     if (!(D2 <= A.half_skin2)) atomicOr(&A.ds->nl_flag[gn3], 1);
 }
 
-// Diagnostics: exact FP64 cells and neighbour counts (strict r^2 < rc^2,
-// minimum image), searched through the buckets of the current generation.
-// An atom missing from its bucket is reported as cell -1.
+// Diagnostics: exact FP64 cells (of the reported grid, side >= rc + skin)
+// and neighbour counts (strict r^2 < rc^2, minimum image), searched through
+// the MD buckets of the current generation. An atom sits in the bucket of
+// its exact MD cell or, after FP32 binning in the substeps, of a neighbour
+// of it; one found in none of these is reported as cell -1.
 __global__ void k_md_diag(AtomArgs A, int *cell_of, int *neigh) {
     const int a = blockIdx.x * blockDim.x + threadIdx.x;
     if (a >= A.na) return;
     const long long gen = (long long)A.ds->step * A.n_md;
     const int g3 = (int)(gen % 3);
     const int na = A.na;
-    int c[3];
-    for (int d = 0; d < 3; ++d) c[d] = exact_cell(A.X[d * na + a], A.nc[d], A.Ld[d]);
-    const int lin = (c[2] * A.nc[1] + c[1]) * A.nc[0] + c[0];
-    bool found = false;
-    {
-        const int b = bucket_of(A, c);
-        const int n = min(A.count[g3][b], A.cap);
-        for (int j = 0; j < n; ++j) found = found || A.slot[g3][(size_t)b * A.cap + j] == a;
+    int c[3], cb[3];
+    for (int d = 0; d < 3; ++d) {
+        c[d] = exact_cell(A.X[d * na + a], A.nc[d], A.Ld[d]);
+        cb[d] = exact_cell(A.X[d * na + a], A.bnc[d], A.Ld[d]);
     }
+    const int lin = (c[2] * A.nc[1] + c[1]) * A.nc[0] + c[0];
+    // Offsets -r..r of a window, without those that alias a nearer one on
+    // a grid of fewer than 2r + 1 cells.
+    auto alias = [&](int o, int d) { return o > A.bnc[d] / 2 || o < -((A.bnc[d] - 1) / 2); };
+    bool found = false;
+    for (int oz = -1; oz <= 1; ++oz)
+        for (int oy = -1; oy <= 1; ++oy)
+            for (int ox = -1; ox <= 1; ++ox) {
+                const int o[3] = {ox, oy, oz};
+                int cc[3];
+                for (int d = 0; d < 3; ++d) cc[d] = wrapi(cb[d] + o[d], A.bnc[d]);
+                const int b = bucket_of(A, cc);
+                const int n = min(A.count[g3][b], A.bcap);
+                for (int j = 0; j < n; ++j) found = found || A.slot[g3][(size_t)b * A.bcap + j] == a;
+            }
     if (cell_of) cell_of[a] = found ? lin : -1;
     if (!neigh) return;
     int count = 0;
     const double xa[3] = {A.X[a], A.X[na + a], A.X[2 * na + a]};
-    // A 5x5x5 block of cells covers any bucket an atom within rc can sit in
-    // after FP32 binning (at most one cell from its exact cell). The block's
-    // buckets are distinct (fold >= 5, or small grids visit each residue
-    // once), so every atom is seen at most once; atoms of folded far cells
-    // fail the distance test.
-    for (int oz = -2; oz <= 2; ++oz)
-        for (int oy = -2; oy <= 2; ++oy)
-            for (int ox = -2; ox <= 2; ++ox) {
+    // A block of MD cells of radius R covers every cell an atom within rc
+    // can be binned in: its exact cell is at most R - 1 away (R = 3 for cells
+    // of side >= rc/2, 2 for side >= rc), plus one for FP32 binning. Its
+    // buckets are distinct once aliased offsets are skipped, so every atom is
+    // seen at most once; atoms of folded far cells fail the distance test.
+    const int R = A.bwin == 5 ? 3 : 2;
+    for (int oz = -R; oz <= R; ++oz)
+        for (int oy = -R; oy <= R; ++oy)
+            for (int ox = -R; ox <= R; ++ox) {
                 const int o[3] = {ox, oy, oz};
+                if (alias(ox, 0) || alias(oy, 1) || alias(oz, 2)) continue;
                 int cc[3];
-                bool dup = false;
-                for (int d = 0; d < 3; ++d) {
-                    cc[d] = wrapi(c[d] + o[d], A.nc[d]);
-                    // skip offsets that alias a nearer one on small grids
-                    if (A.nc[d] < 5 && (o[d] > A.nc[d] / 2 || o[d] < -((A.nc[d] - 1) / 2))) dup = true;
-                }
-                if (dup) continue;
+                for (int d = 0; d < 3; ++d) cc[d] = wrapi(cb[d] + o[d], A.bnc[d]);
                 const int b = bucket_of(A, cc);
-                const int n = min(A.count[g3][b], A.cap);
+                const int n = min(A.count[g3][b], A.bcap);
                 for (int j = 0; j < n; ++j) {
-                    const int q = A.slot[g3][(size_t)b * A.cap + j];
+                    const int q = A.slot[g3][(size_t)b * A.bcap + j];
                     if (q == a) continue;
                     double r2 = 0.0;
                     for (int d = 0; d < 3; ++d) {
@@ -710,7 +732,7 @@ cudaError_t launch_md_prime(const AtomArgs &a, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-template <int TPA>
+template <int TPA, int W>
 cudaError_t launch_substep(const AtomArgs &a, int k, cudaStream_t s) {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((a.na + 4 * (32 / TPA) - 1) / (4 * (32 / TPA)));  // 128 threads, TPA lanes per atom
@@ -721,13 +743,14 @@ cudaError_t launch_substep(const AtomArgs &a, int k, cudaStream_t s) {
     attr[0].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, k_md_substep<TPA, 2>, a, k);
+    return cudaLaunchKernelEx(&cfg, k_md_substep<TPA, 2, W>, a, k);
 }
 
 cudaError_t launch_md_substep(const AtomArgs &a, int k, cudaStream_t s) {
     if (a.na == 0) return cudaSuccess;
     // Above ~64k atoms the 8-lane grid no longer fits the GPU in one wave.
-    return a.na > 65536 ? launch_substep<4>(a, k, s) : launch_substep<8>(a, k, s);
+    if (a.bwin == 5) return a.na > 65536 ? launch_substep<4, 5>(a, k, s) : launch_substep<8, 5>(a, k, s);
+    return a.na > 65536 ? launch_substep<4, 3>(a, k, s) : launch_substep<8, 3>(a, k, s);
 }
 
 cudaError_t launch_md_sort(const AtomArgs &a, cudaStream_t s) {
