@@ -384,7 +384,36 @@ __device__ __noinline__ void build_list(const AtomArgs &A, const float4 *__restr
     in_cell(A, pa, la, t);
     const int nbond = b1 - b0;
     const int partner = lane < nbond ? A.bpart[b0 + lane] : -1;
-    const int total = cell_table<W>(A, g3, cc, t, A.rl2, tab);
+    // 27 coarse cells: lane k < 27 holds cell k's count, bucket and inclusive
+    // prefix in registers, found by a shuffle search; 125 half-size cells:
+    // the prefix table in shared memory, found by a binary search there.
+    int bucket = 0, n = 0, incl = 0, total;
+    if constexpr (W == 3) {
+        if (lane < 27) {
+            const int o[3] = {lane % 3 - 1, (lane / 3) % 3 - 1, lane / 9 - 1};
+            float gap2 = 0.f;
+#pragma unroll
+            for (int d = 0; d < 3; ++d) {
+                const float g = o[d] < 0 ? t[d] : (o[d] > 0 ? A.bh[d] - t[d] : 0.f);
+                gap2 += g * g;
+            }
+            if (gap2 < A.rl2 * 1.001f) {
+                const int c[3] = {wrapi(cc[0] + o[0], A.bnc[0]), wrapi(cc[1] + o[1], A.bnc[1]),
+                                  wrapi(cc[2] + o[2], A.bnc[2])};
+                bucket = bucket_of(A, c);
+                n = min(A.count[g3][bucket], A.bcap);
+            }
+        }
+        incl = n;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int v = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += v;
+        }
+        total = __shfl_sync(0xffffffffu, incl, 31);
+    } else {
+        total = cell_table<W>(A, g3, cc, t, A.rl2, tab);
+    }
     int kept = 0;
     int *__restrict__ out = A.nbr + (size_t)a * NL_MAX;
     for (int t0 = 0; t0 < total; t0 += 32 * NBB) {
@@ -392,9 +421,21 @@ __device__ __noinline__ void build_list(const AtomArgs &A, const float4 *__restr
 #pragma unroll
         for (int u = 0; u < NBB; ++u) {
             const int tc = t0 + 32 * u + lane;
-            int before;
-            const int pos = cand_cell(tab, tc < total ? tc : total - 1, before);
-            q[u] = tc < total ? A.slot[g3][(size_t)tab[128 + pos] * A.bcap + (tc - before)] : -1;
+            int cb, before;
+            if constexpr (W == 3) {
+                int pos = 0;  // first lane whose inclusive count exceeds tc
+#pragma unroll
+                for (int step = 16; step > 0; step >>= 1) {
+                    const int probe = __shfl_sync(0xffffffffu, incl, pos + step - 1);
+                    if (probe <= tc) pos += step;
+                }
+                cb = __shfl_sync(0xffffffffu, bucket, pos & 31);
+                before = __shfl_sync(0xffffffffu, incl - n, pos & 31);
+            } else {
+                const int pos = cand_cell(tab, tc < total ? tc : total - 1, before);
+                cb = tab[128 + pos];
+            }
+            q[u] = tc < total ? A.slot[g3][(size_t)cb * A.bcap + (tc - before)] : -1;
         }
         float4 pq[NBB], lq[NBB];
 #pragma unroll
