@@ -244,3 +244,95 @@ def test_wall_stencil_is_rejected(orc):
     cfg = dict(nx=4, ny=4, nz=4, tau=1.0, walls_z=1)
     with pytest.raises(ValueError):
         orc.interp(cfg, np.zeros((3, 64)), np.array([[1.0], [1.0], [3.5]]))
+
+
+def _static_obs(orc, x, mass):
+    """obs of one oracle step in which nothing can move: fluid at rest, atoms
+    at rest, no Lennard-Jones, no bonds, so x after the step is x exactly and
+    obs[3] is the squared radius of gyration of x itself."""
+    n = 16 ** 3
+    cfg = dict(nx=16, ny=16, nz=16, tau=0.8, gamma=0.5, n_md=4, lj_eps=0.0)
+    f = orc.equilibrium(np.ones(n), np.zeros((3, n)))
+    topo = orc.Topology(np.asarray(mass, float), np.zeros((0, 2)), [], [])
+    _, x2, _, obs = orc.run(cfg, topo, f, x, np.zeros_like(x), 1)
+    assert np.array_equal(x2, x)
+    return obs[0, 3]
+
+
+def test_radius_of_gyration_two_unequal_beads(orc):
+    """Two beads of masses m1, m2 a distance d apart: about the mass-weighted
+    centre, R_g^2 = m1 m2 d^2 / (m1 + m2)^2 (an unweighted centre or an
+    unweighted average would give d^2/4)."""
+    m1, m2, d = 0.7, 1.9, 1.3
+    rng = np.random.default_rng(21)
+    e = rng.standard_normal(3)
+    e /= np.linalg.norm(e)
+    c = np.array([7.2, 8.1, 6.6])
+    x = np.stack([c, c + d * e], axis=1)
+    assert np.isclose(_static_obs(orc, x, [m1, m2]), m1 * m2 * d * d / (m1 + m2) ** 2, rtol=1e-12)
+
+
+@pytest.mark.parametrize("masses", ["equal", "alternating"])
+def test_radius_of_gyration_ring(orc, masses):
+    """n beads on a circle of radius R in a tilted plane: R_g^2 = R^2 whether
+    the masses are equal or alternate (either way the centre of mass is the
+    circle's centre); unwrapped positions past the box edge count as they are."""
+    n, R = 12, 2.5
+    rng = np.random.default_rng(22)
+    a, b = np.linalg.qr(rng.standard_normal((3, 2)))[0].T
+    phi = 2 * np.pi * np.arange(n) / n
+    c = np.array([15.5, 0.3, 8.0])  # the ring crosses y = 0
+    x = c[:, None] + R * (np.cos(phi)[None, :] * a[:, None] + np.sin(phi)[None, :] * b[:, None])
+    mass = np.ones(n) if masses == "equal" else np.where(np.arange(n) % 2 == 0, 0.6, 1.8)
+    assert np.isclose(_static_obs(orc, x, mass), R * R, rtol=1e-12)
+
+
+def test_radius_of_gyration_is_translation_invariant(orc, c1):
+    _, inp = c1
+    x = inp["x"][:, :60]
+    mass = np.random.default_rng(23).uniform(0.5, 2.0, 60)
+    r1 = _static_obs(orc, x, mass)
+    r2 = _static_obs(orc, x + np.array([[3.25], [-1.5], [0.75]]), mass)
+    assert np.isclose(r1, r2, rtol=1e-12)
+    # and equals the mass-weighted definition written out here
+    cm = (x * mass).sum(1) / mass.sum()
+    assert np.isclose(r1, (mass * ((x - cm[:, None]) ** 2).sum(0)).sum() / mass.sum(), rtol=1e-12)
+
+
+@pytest.mark.parametrize("m", [0.5, 2.5])
+def test_single_atom_drag_with_mass(orc, m):
+    """The friction gamma (u - v) is a force (gamma in mass per time): an atom
+    of mass m relaxes u0 - v by (1 - gamma/(2 n_md m)) per half-kick, so its
+    impulse after one step is m u0 [1 - (1 - gamma/(2 n_md m))^(2 n_md)]; a
+    per-mass friction rate would drop the m inside."""
+    gamma, u0, n_md = 0.5, 1e-3, 8
+    cfg = dict(nx=4, ny=4, nz=4, tau=0.8, gamma=gamma, n_md=n_md)
+    u = np.zeros((3, 64))
+    u[0] = u0
+    f = orc.equilibrium(np.ones(64), u)
+    topo = orc.Topology(np.array([m]), np.zeros((0, 2)), [], [])
+    _, _, v2, obs = orc.run(cfg, topo, f, np.array([[1.3], [2.1], [0.7]]), np.zeros((3, 1)), 1)
+    vexp = u0 * (1 - (1 - gamma / (2 * n_md * m)) ** (2 * n_md))
+    assert np.isclose(v2[0, 0], vexp, rtol=1e-13)
+    assert np.isclose(obs[0, 0], m * vexp, rtol=1e-13)
+
+
+def test_total_momentum_with_unequal_masses(orc):
+    """sum f c + sum m v is conserved with random masses in [0.5, 2] (no body
+    force): the fluid receives exactly the impulse the atoms lose."""
+    cfg = dict(synth._COMMON, nx=12, ny=12, nz=12, tau=0.8, gamma=0.5, n_md=128,
+               chains=[dict(n=80, centre="box", radius=None)])
+    inp = synth.inputs(cfg, 3)
+    rng = np.random.default_rng(24)
+    mass = rng.uniform(0.5, 2.0, inp["x"].shape[1])
+    topo = orc.Topology(mass, inp["bonds"], inp["bond_k"], inp["bond_r0"])
+    u = 0.01 * rng.standard_normal((3, 12 ** 3))
+    f = orc.equilibrium(np.ones(12 ** 3), u)
+    v = 0.05 * rng.standard_normal(inp["x"].shape)
+    _, j0 = orc.moments(f)
+    P0 = j0.sum(1) + (mass * v).sum(1)
+    f2, _, v2, _ = orc.run(cfg, topo, f, inp["x"], v, 4)
+    _, j1 = orc.moments(f2)
+    P1 = j1.sum(1) + (mass * v2).sum(1)
+    assert np.allclose(P1, P0, rtol=0, atol=1e-12)
+    assert np.abs((mass * (v2 - v)).sum(1)).max() > 1e-4  # the coupling moved momentum
