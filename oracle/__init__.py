@@ -34,7 +34,8 @@ class _Params(C.Structure):
                 ("cell_min", C.c_double),
                 ("forcing", C.c_int), ("force_amp", C.c_double),
                 ("force_dir", C.c_int), ("force_wave_axis", C.c_int),
-                ("walls_z", C.c_int), ("brute_force", C.c_int)]
+                ("walls_z", C.c_int), ("brute_force", C.c_int),
+                ("kT", C.c_double), ("seed", C.c_uint64), ("step0", C.c_int64)]
 
 
 class _Topology(C.Structure):
@@ -81,7 +82,8 @@ def params(cfg, brute_force=False):
                    rcut + float(cfg.get("skin", 0.0)),
                    forcing, float(cfg.get("force_amp", 0.0)),
                    int(cfg.get("force_dir", 0)), int(cfg.get("force_wave_axis", 1)),
-                   int(cfg.get("walls_z", 0)), int(bool(brute_force)))
+                   int(cfg.get("walls_z", 0)), int(bool(brute_force)),
+                   float(cfg.get("kT", 0.0)), int(cfg.get("seed", 0)), int(cfg.get("step0", 0)))
 
 
 class Topology:
@@ -144,6 +146,31 @@ def collide_node(tau, f, F):
     out = np.zeros(Q)
     lib().orc_collide_node(C.c_double(tau), _d(f), _d(F), _d(out))
     return out
+
+
+def philox4x32_10(ctr, key):
+    """Philox4x32-10 block of the 4-word counter and 2-word key."""
+    c = (C.c_uint32 * 4)(*[int(v) & 0xFFFFFFFF for v in ctr])
+    k = (C.c_uint32 * 2)(*[int(v) & 0xFFFFFFFF for v in key])
+    out = (C.c_uint32 * 4)()
+    lib().orc_philox4x32_10(c, k, out)
+    return [int(v) for v in out]
+
+
+def mode_basis():
+    """D3Q19 moment basis E (19 modes x 19 speeds) and norms b_k = sum w E^2."""
+    E = np.zeros((Q, Q))
+    b = np.zeros(Q)
+    lib().orc_mode_basis(_d(E), _d(b))
+    return E, b
+
+
+def node_noise(cfg, node, step):
+    """The thermal noise xi (19,) the oracle adds at a node and step."""
+    p = params(cfg)
+    xi = np.zeros(Q)
+    lib().orc_node_noise(C.byref(p), C.c_int64(int(node)), C.c_int64(int(step)), _d(xi))
+    return xi
 
 
 def body_force(cfg):

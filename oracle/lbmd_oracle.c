@@ -36,8 +36,17 @@
  *      distances use the minimum image.
  *  R10 Optional z walls: half-way bounce-back at z = -1/2 and z = nz - 1/2.
  *      Atoms must keep their interpolation stencil inside 0..nz-1.
- *  R11 The thermal noise xi_i of the fluctuating LB (Sec. 2.2) is not part of
- *      this deterministic step.
+ *  R11 The thermal noise xi_i of the fluctuating LB (Sec. 2.2, the source term
+ *      S_i = p_i + xi_i of Eq. 1) is added after the collision when kT > 0:
+ *      Gaussian noise on the 15 non-conserved modes of the weighted-orthogonal
+ *      D3Q19 moment basis below, each with variance mu b_k (1 - (1 - omega)^2),
+ *      mu = rho0 kT / c_s^2 (the fluctuation-dissipation amplitude of a BGK
+ *      relaxation 1 - omega; rho0 rather than the local density), so that at
+ *      rest every mode holds mu b_k and the fluid velocity kT/rho0 per
+ *      component. Mass and momentum get no noise. Random numbers: Philox4x32-10
+ *      (Salmon et al., SC'11) with counter (node, call, step low, step high)
+ *      and key (seed low, seed high); uniforms ((w >> 8) + 1/2) 2^-24; normals
+ *      by the Box-Muller transform.
  */
 #define _DEFAULT_SOURCE
 #include <math.h>
@@ -78,6 +87,9 @@ typedef struct {
     int force_dir, force_wave_axis;
     int walls_z;
     int brute_force;                  /* 1: all-pairs search instead of cells */
+    double kT;                        /* thermal energy of the fluctuating LB (0: no noise) */
+    uint64_t seed;                    /* key of the noise's random numbers */
+    int64_t step0;                    /* step index of the first step of a run */
 } orc_params;
 
 typedef struct {
@@ -177,6 +189,104 @@ void orc_collide_node(double tau, const double *f /* Q */, const double F[3], do
     for (int d = 0; d < 3; ++d) u[d] = (j[d] + 0.5 * F[d]) / rho;
     for (int i = 0; i < Q; ++i)
         out[i] = f[i] - omega * (f[i] - equilibrium(i, rho, u)) + guo_source(i, omega, u, F);
+}
+
+/* ---------------------------------------------------------------------- */
+/* Thermal noise (R11). Philox4x32-10 as published: ten rounds of
+ * (c0, c1, c2, c3) -> (hi(M1 c2) ^ c1 ^ k0, lo(M1 c2), hi(M0 c0) ^ c3 ^ k1,
+ * lo(M0 c0)) with the key advanced by the Weyl constants between rounds. */
+void orc_philox4x32_10(const uint32_t ctr_in[4], const uint32_t key_in[2], uint32_t out[4]) {
+    const uint32_t M0 = 0xD2511F53u, M1 = 0xCD9E8D57u, W0 = 0x9E3779B9u, W1 = 0xBB67AE85u;
+    uint32_t c[4] = {ctr_in[0], ctr_in[1], ctr_in[2], ctr_in[3]};
+    uint32_t k0 = key_in[0], k1 = key_in[1];
+    for (int r = 0; r < 10; ++r) {
+        uint64_t p0 = (uint64_t)M0 * c[0], p1 = (uint64_t)M1 * c[2];
+        uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+        uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+        uint32_t n0 = hi1 ^ c[1] ^ k0, n2 = hi0 ^ c[3] ^ k1;
+        c[0] = n0;
+        c[1] = lo1;
+        c[2] = n2;
+        c[3] = lo0;
+        k0 += W0;
+        k1 += W1;
+    }
+    for (int i = 0; i < 4; ++i) out[i] = c[i];
+}
+
+/* Mode k of the D3Q19 moment basis at speed i: polynomials in c, orthogonal
+ * under the weights w_i. 0: 1; 1-3: c_x, c_y, c_z; 4: c^2 - 1; 5: 3c_x^2 - c^2;
+ * 6: c_y^2 - c_z^2; 7-9: c_x c_y, c_y c_z, c_x c_z; 10-12: (3c^2 - 5) c_x,y,z;
+ * 13: (c_y^2 - c_z^2) c_x; 14: (c_z^2 - c_x^2) c_y; 15: (c_x^2 - c_y^2) c_z;
+ * 16: 3c^4 - 6c^2 + 1; 17: (2c^2 - 3)(3c_x^2 - c^2); 18: (2c^2 - 3)(c_y^2 - c_z^2). */
+static double mode_value(int k, int i) {
+    const double x = CX[i], y = CY[i], z = CZ[i];
+    const double c2 = x * x + y * y + z * z;
+    switch (k) {
+    case 0: return 1.0;
+    case 1: return x;
+    case 2: return y;
+    case 3: return z;
+    case 4: return c2 - 1.0;
+    case 5: return 3.0 * x * x - c2;
+    case 6: return y * y - z * z;
+    case 7: return x * y;
+    case 8: return y * z;
+    case 9: return x * z;
+    case 10: return (3.0 * c2 - 5.0) * x;
+    case 11: return (3.0 * c2 - 5.0) * y;
+    case 12: return (3.0 * c2 - 5.0) * z;
+    case 13: return (y * y - z * z) * x;
+    case 14: return (z * z - x * x) * y;
+    case 15: return (x * x - y * y) * z;
+    case 16: return 3.0 * c2 * c2 - 6.0 * c2 + 1.0;
+    case 17: return (2.0 * c2 - 3.0) * (3.0 * x * x - c2);
+    default: return (2.0 * c2 - 3.0) * (y * y - z * z);
+    }
+}
+
+/* E[k*Q + i] = mode k at speed i; b[k] = sum_i w_i E_ki^2. */
+void orc_mode_basis(double *E, double *b) {
+    for (int k = 0; k < Q; ++k) {
+        b[k] = 0.0;
+        for (int i = 0; i < Q; ++i) {
+            E[k * Q + i] = mode_value(k, i);
+            b[k] += weight(i) * E[k * Q + i] * E[k * Q + i];
+        }
+    }
+}
+
+/* The 16 standard normals of a node and step: four Philox blocks, each
+ * giving two Box-Muller pairs from its words (w0, w1) and (w2, w3). */
+static void node_normals(uint64_t seed, int64_t node, int64_t step, double n[16]) {
+    const uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+    for (int call = 0; call < 4; ++call) {
+        const uint32_t ctr[4] = {(uint32_t)node, (uint32_t)call, (uint32_t)step, (uint32_t)((uint64_t)step >> 32)};
+        uint32_t w[4];
+        orc_philox4x32_10(ctr, key, w);
+        for (int p = 0; p < 2; ++p) {
+            const double u1 = ((double)(w[2 * p] >> 8) + 0.5) * (1.0 / 16777216.0);
+            const double u2 = ((double)(w[2 * p + 1] >> 8) + 0.5) * (1.0 / 16777216.0);
+            const double r = sqrt(-2.0 * log(u1));
+            n[4 * call + 2 * p] = r * cos(2.0 * 3.14159265358979323846 * u2);
+            n[4 * call + 2 * p + 1] = r * sin(2.0 * 3.14159265358979323846 * u2);
+        }
+    }
+}
+
+/* xi_i = w_i sum_{k=4..18} E_ki sqrt(mu (1 - (1 - omega)^2) / b_k) n_{k-4}. */
+void orc_node_noise(const orc_params *p, int64_t node, int64_t step, double *xi /* Q */) {
+    double E[Q * Q], b[Q], n[16];
+    orc_mode_basis(E, b);
+    node_normals(p->seed, node, step, n);
+    const double omega = 1.0 / p->tau;
+    const double mu = 3.0 * p->rho0 * p->kT;
+    const double g = 1.0 - omega;
+    for (int i = 0; i < Q; ++i) {
+        double s = 0.0;
+        for (int k = 4; k < Q; ++k) s += E[k * Q + i] * sqrt(mu * (1.0 - g * g) / b[k]) * n[k - 4];
+        xi[i] = weight(i) * s;
+    }
 }
 
 /* Body force g(x) (not in the paper; the workload's forcing): uniform or
@@ -587,11 +697,12 @@ static int check_params(const orc_params *p, const orc_topology *t) {
         p->force_wave_axis < 0 || p->force_wave_axis > 2)
         return ORC_ERR_ARG;
     if (p->walls_z && p->nz < 2) return ORC_ERR_ARG;
+    if (!(p->kT >= 0.0)) return ORC_ERR_ARG;
     return ORC_OK;
 }
 
 static int step_once(const orc_params *p, const orc_topology *t, const adjacency *adj, work *w,
-                     double *f, double *x, double *v, double *obs) {
+                     double *f, double *x, double *v, double *obs, int64_t step) {
     const size_t N = n_nodes(p);
     const int na = t->n_atoms;
     int err;
@@ -657,6 +768,11 @@ static int step_once(const orc_params *p, const orc_topology *t, const adjacency
         for (int i = 0; i < Q; ++i) fl[i] = f[(size_t)i * N + k];
         for (int d = 0; d < 3; ++d) F[d] = w->g[d * N + k] + w->G[d * N + k];
         orc_collide_node(p->tau, fl, F, out);
+        if (p->kT > 0.0) {
+            double xi[Q];
+            orc_node_noise(p, (int64_t)k, step, xi);
+            for (int i = 0; i < Q; ++i) out[i] += xi[i];
+        }
         for (int i = 0; i < Q; ++i) w->fs[(size_t)i * N + k] = out[i];
     }
 
@@ -703,7 +819,8 @@ int orc_run(const orc_params *p, const orc_topology *t, double *f, double *x, do
     }
     work w;
     err = alloc_work(p, t->n_atoms, &w);
-    for (int s = 0; s < n_steps && !err; ++s) err = step_once(p, t, &adj, &w, f, x, v, obs ? obs + 4 * s : NULL);
+    for (int s = 0; s < n_steps && !err; ++s)
+        err = step_once(p, t, &adj, &w, f, x, v, obs ? obs + 4 * s : NULL, p->step0 + s);
     free_work(&w);
     free_adjacency(&adj);
     return err;
