@@ -43,6 +43,19 @@ WORKLOADS = {
     "channel10x20k_lattice512": dict(_COMMON, nx=512, ny=512, nz=512, tau=0.8, u_sigma=0.0,
                                      forcing="poiseuille", force_amp=1e-6, walls_z=1,
                                      chains="grid10", steps=500),
+    # The same ten globules in a shallower 256 x 256 x 64 channel: the solute
+    # of the 512^3 channel on a lattice 32x smaller (profiling of the solute
+    # kernels on a few GB of device memory).
+    "channel10x20k_lattice256x256x64": dict(_COMMON, nx=256, ny=256, nz=64, tau=0.8, u_sigma=0.0,
+                                            forcing="poiseuille", force_amp=1e-6, walls_z=1,
+                                            chains="grid10", steps=500),
+    # A z-channel small enough for the oracle that still takes the 512^3
+    # channel's code path: more than 65,536 atoms, a box side above 166 (the
+    # coarse pair-search grid), walls, and two flat chains whose stencils touch
+    # the first and the last fluid plane pair (z = 0.5 and z = nz - 1.5).
+    "channel4x17k_lattice176x48x48": dict(_COMMON, nx=176, ny=48, nz=48, tau=0.8, u_sigma=0.0,
+                                          forcing="poiseuille", force_amp=1e-6, walls_z=1,
+                                          chains="channel4", steps=2),
 }
 
 
@@ -113,13 +126,15 @@ def _min_image(d, box):
 
 
 def self_avoiding_chain(n, seed, start, box, step=0.5, exclude=0.4, radius=None,
-                        centre=None, grid=None, trials=32, max_rounds=64):
+                        centre=None, grid=None, trials=32, max_rounds=64, planar=False):
     """Self-avoiding random walk of n beads with fixed step length: each new
     bead is placed at a uniformly random direction from the previous one and
     rejected when it comes within `exclude` of any earlier bead (minimum image,
     periodic box) or, if `radius` is given, leaves the sphere of that radius
-    around `centre`. Dead ends are left by backtracking a few beads. Returns
-    unwrapped positions (3, n)."""
+    around `centre`. planar=True keeps the walk in the plane z = start z and
+    directed along +x (directions drawn in the half plane x > 0, so the walk
+    never traps itself). Dead ends are left by backtracking a few beads.
+    Returns unwrapped positions (3, n)."""
     rng = np.random.Generator(np.random.PCG64(seed))
     box = np.asarray(box, dtype=np.float64)
     if grid is None:
@@ -133,6 +148,9 @@ def self_avoiding_chain(n, seed, start, box, step=0.5, exclude=0.4, radius=None,
         placed = False
         for _ in range(max_rounds):
             dirs = rng.normal(size=(trials, 3))
+            if planar:
+                dirs[:, 2] = 0.0
+                dirs[:, 0] = np.abs(dirs[:, 0])
             dirs /= np.linalg.norm(dirs, axis=1, keepdims=True)
             cand = prev[None, :] + step * dirs
             ok = np.ones(trials, dtype=bool)
@@ -206,13 +224,20 @@ def solute(cfg, seed):
     elif chains == "grid10":
         specs = [dict(n=20000, c=np.array([(i + 0.5) * box[0] / 5, (j + 0.5) * box[1] / 2, box[2] / 2]),
                       radius=20.0) for j in range(2) for i in range(5)]
+    elif chains == "channel4":
+        # Four 17k-bead globules (radius 19.5) along x in the mid-plane, and two
+        # flat 300-bead walks at z = 0.5 and z = nz - 1.5 next to the walls.
+        specs = [dict(n=17000, c=np.array([(i + 0.5) * box[0] / 4, box[1] / 2, box[2] / 2]), radius=19.5)
+                 for i in range(4)]
+        specs += [dict(n=300, c=np.array([box[0] / 8, box[1] / 2, z]), radius=None, planar=True)
+                  for z in (0.5, box[2] - 1.5)]
     else:
         specs = [dict(n=c["n"], c=centre if c["centre"] == "box" else np.asarray(c["centre"]),
                       radius=c["radius"]) for c in chains]
     off = 0
     for ci, s in enumerate(specs):
         x = self_avoiding_chain(s["n"], seed * 1000 + ci, s["c"], box, step=step, exclude=excl,
-                                radius=s["radius"], centre=s["c"], grid=grid)
+                                radius=s["radius"], centre=s["c"], grid=grid, planar=s.get("planar", False))
         xs.append(x)
         bonds.append(_chain_bonds(off, s["n"]))
         k.append(np.full(s["n"] - 1, cfg["bond_k"]))

@@ -74,3 +74,54 @@ def assert_within(errs, floors, tol=1e-5):
     for k, e in errs.items():
         bound = max(tol, floors.get(k, 0.0))
         assert e <= bound, f"{k}: error {e:.3e} > bound {bound:.3e} (floor {floors.get(k, 0.0):.3e})"
+
+
+# Factor on the FP32 floor in the per-step bounds. The floor is the oracle's
+# response to ONE rounding of the step's inputs; the CUDA path also rounds
+# inside the step (velocities at every half-kick, pair forces at every
+# substep), yet over the suite's 604 per-field, per-step comparisons the
+# worst error / floor among those where the floor term binds (error > 1e-5)
+# was 1.09 (random-mass chain, v). FLOOR_FACTOR = 2 keeps that margin; the
+# errors did not need the sqrt(n_md) ~ 11 random-walk factor once assumed.
+FLOOR_FACTOR = 2.0
+
+
+def floor_bound(cfg, floor, tol=1e-5):
+    return max(tol, FLOOR_FACTOR * floor)
+
+
+def step_errors(orc, cfg, s, fo, xo, vo):
+    return dict(f=rel_linf(s["f"], fo), u=rel_linf(s["u"], velocity(orc, cfg, fo)), x=rel_linf(s["x"], xo),
+                v=rel_linf(s["v"], vo))
+
+
+def report_ratios(name, errs, floors):
+    """One line per comparison: error, floor and error / floor per field (the
+    measurements behind FLOOR_FACTOR)."""
+    print("RATIO", name, " ".join(f"{k}: err {errs[k]:.3e} floor {floors.get(k, 0.0):.3e} "
+                                  f"ratio {errs[k] / max(floors.get(k, 0.0), 1e-300):.3g}" for k in errs))
+
+
+def teacher_forced(orc, cfg, inp, steps, name, h=None):
+    """At every step: oracle step from the GPU's current state, compared with
+    the GPU's own next state and with the FP32 floor of that step. Returns the
+    steps done and the worst error / floor_bound per field."""
+    h = make(cfg, inp) if h is None else h
+    topo = orc.Topology(inp["mass"], inp["bonds"], inp["bond_k"], inp["bond_r0"])
+    worst = dict(f=0.0, u=0.0, x=0.0, v=0.0)
+    s = lbmd.lbmd_get_fields(h, f=True, x=True, v=True)
+    done = 0
+    for n in range(steps):
+        floors, (fo, xo, vo) = fp32_floor(orc, cfg, topo, s["f"].astype(np.float64), s["x"],
+                                          s["v"].astype(np.float64), 1, seed=n)
+        lbmd.lbmd_step(h, 1)
+        s = lbmd.lbmd_get_fields(h, f=True, u=True, x=True, v=True)
+        if not (np.all(np.isfinite(fo)) and np.all(np.isfinite(vo))):
+            break
+        errs = step_errors(orc, cfg, s, fo, xo, vo)
+        report_ratios(f"{name} step {n}", errs, floors)
+        for k in worst:
+            worst[k] = max(worst[k], errs[k] / floor_bound(cfg, floors[k]))
+        done += 1
+    lbmd.lbmd_check(h)  # no bucket or neighbour-list overflow, no non-finite value, no wall crossing
+    return worst, done

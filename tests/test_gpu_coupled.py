@@ -13,7 +13,8 @@ import numpy as np
 import pytest
 
 from paper_2305_05025_gb300 import build, lbmd, synth
-from gpu_helpers import assert_within, fp32_floor, make, oracle_start, rel_linf, velocity
+from gpu_helpers import (assert_within, floor_bound, fp32_floor, make, oracle_start, rel_linf, report_ratios,
+                         step_errors, teacher_forced, velocity)
 
 pytestmark = pytest.mark.gpu
 
@@ -76,34 +77,6 @@ def test_single_atom_in_uniform_flow(n_md):
     assert abs(m1 - m0) < 1e-8  # FP32 rounding of 64 nodes' populations
 
 
-def _teacher_forced(orc, cfg, inp, steps):
-    """At every step: oracle step from the GPU's current state, compared with
-    the GPU's own next state and with the FP32 floor of that step. Returns the
-    steps done and the worst ratio error / max(1e-5, sqrt(n_md) floor) per
-    field: the floor models one FP32 rounding of the step's inputs, while the
-    CUDA path rounds again in each of its n_md substeps, and independent
-    roundings add up like a random walk."""
-    h = make(cfg, inp)
-    topo = orc.Topology(inp["mass"], inp["bonds"], inp["bond_k"], inp["bond_r0"])
-    worst = dict(f=0.0, u=0.0, x=0.0, v=0.0)
-    s = lbmd.lbmd_get_fields(h, f=True, x=True, v=True)
-    done = 0
-    for n in range(steps):
-        floors, (fo, xo, vo) = fp32_floor(orc, cfg, topo, s["f"].astype(np.float64), s["x"],
-                                          s["v"].astype(np.float64), 1, seed=n)
-        lbmd.lbmd_step(h, 1)
-        s = lbmd.lbmd_get_fields(h, f=True, u=True, x=True, v=True)
-        if not (np.all(np.isfinite(fo)) and np.all(np.isfinite(vo))):
-            break
-        errs = dict(f=rel_linf(s["f"], fo), u=rel_linf(s["u"], velocity(orc, cfg, fo)), x=rel_linf(s["x"], xo),
-                    v=rel_linf(s["v"], vo))
-        for k in worst:
-            worst[k] = max(worst[k], errs[k] / max(1e-5, np.sqrt(cfg["n_md"]) * floors[k]))
-        done += 1
-    lbmd.lbmd_check(h)  # no bucket or neighbour-list overflow, no non-finite value
-    return worst, done
-
-
 @pytest.mark.parametrize("skin", [0.0, 0.3])
 def test_one_coupled_step_matches_oracle(orc, c1, skin):
     cfg, inp = c1
@@ -115,7 +88,7 @@ def test_one_coupled_step_matches_oracle(orc, c1, skin):
     floors, (fo, xo, vo) = fp32_floor(orc, cfg, topo, f, x, v, 1)
     errs = dict(f=rel_linf(s["f"], fo), u=rel_linf(s["u"], velocity(orc, cfg, fo)), x=rel_linf(s["x"], xo),
                 v=rel_linf(s["v"], vo))
-    print("one step: errors", errs, "floors", floors)
+    report_ratios(f"chain500 one step skin {skin}", errs, floors)
     assert errs["f"] < TOL and errs["x"] < TOL and errs["u"] < TOL
     assert_within(errs, floors)
 
@@ -128,7 +101,7 @@ def test_teacher_forced_100_steps_chain500(orc, c1):
     exchange stable once the chain is dense (gamma = 0.5 diverges near step
     20, in the oracle too)."""
     cfg, inp = c1
-    worst, done = _teacher_forced(orc, dict(cfg, gamma=0.05, skin=0.3), inp, 100)
+    worst, done = teacher_forced(orc, dict(cfg, gamma=0.05, skin=0.3), inp, 100, "chain500 gamma 0.05")
     assert done == 100
     print("teacher-forced worst error / bound:", worst)
     for k, r in worst.items():
@@ -137,7 +110,7 @@ def test_teacher_forced_100_steps_chain500(orc, c1):
 
 def test_teacher_forced_literal_gamma(orc, c1):
     cfg, inp = c1
-    worst, done = _teacher_forced(orc, cfg, inp, 12)
+    worst, done = teacher_forced(orc, cfg, inp, 12, "chain500 gamma 0.5")
     print("gamma 0.5 teacher-forced worst error / bound:", worst, "steps", done)
     assert done == 12
     for k, r in worst.items():
@@ -161,7 +134,7 @@ def test_free_running_harmonic_chain_100_steps(orc, skin):
     floors, (fo, xo, vo) = fp32_floor(orc, cfg, topo, f, x, v, 100)
     errs = dict(f=rel_linf(s["f"], fo), u=rel_linf(s["u"], velocity(orc, cfg, fo)), x=rel_linf(s["x"], xo),
                 v=rel_linf(s["v"], vo))
-    print("harmonic chain, 100 steps: errors", errs, "floors", floors)
+    report_ratios(f"harmonic chain 100 steps free-running skin {skin}", errs, floors)
     assert errs["f"] < TOL and errs["x"] < TOL
     assert_within(errs, floors)
 

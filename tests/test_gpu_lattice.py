@@ -70,13 +70,26 @@ def test_walls_poiseuille_matches_oracle(orc):
     assert rel_linf(g["u"], velocity(orc, cfg, fo)) < TOL
 
 
+# The 16-bit stores run the node-pair kernel (even nx); FP32 the node kernel
+# on the same cases. Bounds: FP32 1e-5 on f and u; FP16 and BF16 their
+# storage resolution of delta f (2^-11 and 2^-8 relative) on delta f and u.
+@pytest.mark.parametrize("store,bound", [("f32", TOL), ("f16", 2e-3), ("bf16", 2e-2)])
 @pytest.mark.parametrize("nx", [70, 96])  # pair kernel: row of 35 pairs (partial warp) and of 48 (warp edge)
-def test_pair_kernel_matches_oracle(orc, nx):
-    cfg = _cfg(nx=nx, ny=5, nz=4, tau=0.7, walls_z=1, forcing="kolmogorov", force_amp=1e-4, force_wave_axis=2)
+def test_pair_kernel_matches_oracle(orc, nx, store, bound):
+    cfg = _cfg(nx=nx, ny=5, nz=4, tau=0.7, walls_z=1, forcing="kolmogorov", force_amp=1e-4, force_wave_axis=2,
+               store=store)
     inp = lattice_inputs((nx, 5, 4), 0.01, 8)
     g, fo = _free_run(orc, cfg, inp, 40)
-    assert rel_linf(g["f"], fo) < TOL
-    assert rel_linf(g["u"], velocity(orc, cfg, fo)) < TOL
+    w = np.array([1 / 3] + [1 / 18] * 6 + [1 / 36] * 12)[:, None]
+    df_err = rel_linf(g["f"] - w, fo - w)
+    u_err = rel_linf(g["u"], velocity(orc, cfg, fo))
+    print(f"pair kernel nx={nx} {store}: delta f {df_err:.3e}, u {u_err:.3e}")
+    if store == "f32":
+        # f crosses the ABI in FP32: delta f recovered from it carries the
+        # rounding of f itself, so FP32 is held to 1e-5 on f and u.
+        assert rel_linf(g["f"], fo) < TOL and u_err < TOL
+    else:
+        assert df_err < bound and u_err < bound
 
 
 def test_kolmogorov_along_x_matches_oracle(orc):

@@ -12,7 +12,7 @@ import numpy as np
 import pytest
 
 from paper_2305_05025_gb300 import build, lbmd, synth
-from gpu_helpers import fp32_floor, make, rel_linf, velocity
+from gpu_helpers import floor_bound, fp32_floor, make, rel_linf, report_ratios, step_errors, velocity
 
 pytestmark = pytest.mark.gpu
 
@@ -61,10 +61,10 @@ def test_globule20k_lattice128_teacher_forced(orc):
         lbmd.lbmd_step(h, 1)
         s = _fields(h)
         _table(f"128^3 step {n}", s, fo, xo, vo, cfg, orc)
-        errs = dict(f=rel_linf(s["f"], fo), u=rel_linf(s["u"], velocity(orc, cfg, fo)), x=rel_linf(s["x"], xo),
-                    v=rel_linf(s["v"], vo))
+        errs = step_errors(orc, cfg, s, fo, xo, vo)
+        report_ratios(f"globule20k 128^3 step {n}", errs, floors)
         for key, e in errs.items():
-            bound = max(1e-5, np.sqrt(cfg["n_md"]) * floors[key])
+            bound = floor_bound(cfg, floors[key])
             assert e <= bound, (n, key, e, bound)
     lbmd.lbmd_check(h)
 
@@ -100,8 +100,9 @@ def test_trimer60k_lattice256_storage_formats(orc):
         s = _fields(h)
         errs = _table(f"256^3 trimer {store}", s, fo, xo, vo, cfg, orc)
         if store == "f32":
-            assert rel_linf(s["f"], fo) <= max(1e-5, np.sqrt(cfg["n_md"]) * floors["f"])
-            assert errs["x"][0] <= max(1e-5, np.sqrt(cfg["n_md"]) * floors["x"])
+            report_ratios("trimer60k 256^3 f32 one step", step_errors(orc, cfg, s, fo, xo, vo), floors)
+            assert rel_linf(s["f"], fo) <= floor_bound(cfg, floors["f"])
+            assert errs["x"][0] <= floor_bound(cfg, floors["x"])
         else:
             assert errs["df"][0] <= bounds[store] and errs["u"][0] <= bounds[store]
             assert errs["x"][0] <= 1e-5
