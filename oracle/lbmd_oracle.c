@@ -45,8 +45,9 @@
  *      rest every mode holds mu b_k and the fluid velocity kT/rho0 per
  *      component. Mass and momentum get no noise. Random numbers: Philox4x32-10
  *      (Salmon et al., SC'11) with counter (node, call, step low, step high)
- *      and key (seed low, seed high); uniforms ((w >> 8) + 1/2) 2^-24; normals
- *      by the Box-Muller transform.
+ *      and key (seed low, seed high); uniforms ((w >> 9) + 1/2) 2^-23 (exact
+ *      in FP32 as in FP64, so a single-precision implementation draws the
+ *      same uniforms); normals by the Box-Muller transform.
  */
 #define _DEFAULT_SOURCE
 #include <math.h>
@@ -265,8 +266,8 @@ static void node_normals(uint64_t seed, int64_t node, int64_t step, double n[16]
         uint32_t w[4];
         orc_philox4x32_10(ctr, key, w);
         for (int p = 0; p < 2; ++p) {
-            const double u1 = ((double)(w[2 * p] >> 8) + 0.5) * (1.0 / 16777216.0);
-            const double u2 = ((double)(w[2 * p + 1] >> 8) + 0.5) * (1.0 / 16777216.0);
+            const double u1 = ((double)(w[2 * p] >> 9) + 0.5) * (1.0 / 8388608.0);
+            const double u2 = ((double)(w[2 * p + 1] >> 9) + 0.5) * (1.0 / 8388608.0);
             const double r = sqrt(-2.0 * log(u1));
             n[4 * call + 2 * p] = r * cos(2.0 * 3.14159265358979323846 * u2);
             n[4 * call + 2 * p + 1] = r * sin(2.0 * 3.14159265358979323846 * u2);
