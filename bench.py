@@ -4,12 +4,14 @@ A step is one coupled lattice-Boltzmann / MD time step (dense stream-collide
 of every node, interpolation at every atom, n_md velocity-Verlet substeps,
 spread-back, sparse fix-up), launched as one CUDA graph through the C ABI.
 
-Default workload: 128^3 periodic lattice, tau 0.6, Kolmogorov forcing 1e-5,
-20,000-bead synthetic globule (radius 20), FP32 populations, n_md = 128.
+Default workload: the 512^3 z-channel (bounce-back walls, Poiseuille forcing
+1e-6, tau 0.8) with ten 20,000-bead synthetic globules (200,000 atoms),
+n_md = 128. Both FP16 shifted storage (the headline `value`) and FP32 storage
+are timed on it, on the same GPU, and reported on one line.
 Metric: coupled MLUPS = nodes x steps / time (whole job, all ranks).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                  [--workload NAME] [--store f32|f16|bf16]
+                  [--workload NAME] [--store f16,f32]
 
 N > 1 runs under torchrun: every rank simulates its own replica (independent
 runs; no collective on the data path), timed between barriers, max over ranks.
@@ -30,7 +32,7 @@ sys.path.insert(0, ROOT)
 
 from paper_2305_05025_gb300 import synth  # noqa: E402
 
-DEFAULT_WORKLOAD = "globule20k_lattice128"
+DEFAULT_WORKLOAD = "channel10x20k_lattice512"
 # Choices the workload description leaves open: n_md resolves the LJ
 # repulsion, gamma keeps the explicit friction exchange stable once the
 # globule is dense, skin sets how long a neighbour list lasts.
@@ -148,55 +150,105 @@ class Clocks:
                        "reasons": reasons, "samples": len(rows)}
 
 
-def run_reference(args, cfg):
-    """The FP64 oracle on the host cores: each step is one full coupled step of
-    the workload (single thread)."""
+def _sub_box(cfg, inp, chain, side=48):
+    """The atoms of one chain (the first `chain` atoms of the solute, with their
+    bonds) moved to the centre of a side^3 box with the workload's walls and
+    forcing: one globule of the workload, for the oracle's solute sample."""
+    n = chain
+    x = inp["x"][:, :n]
+    x = x - x.mean(1, keepdims=True) + side / 2.0
+    b = inp["bonds"]
+    keep = (b[:, 0] < n) & (b[:, 1] < n)
+    sub = dict(cfg, nx=side, ny=side, nz=side)
+    rho, u = synth.velocity_field((side, side, side), 0.0, 1, cfg.get("rho0", 1.0))
+    return sub, dict(rho=rho, u=u, x=x, v=inp["v"][:, :n], mass=inp["mass"][:n], bonds=b[keep],
+                     bond_k=inp["bond_k"][keep], bond_r0=inp["bond_r0"][keep])
+
+
+def oracle_step_seconds(cfg, inp):
+    """Seconds the FP64 oracle (single thread) takes for one coupled step of the
+    workload, and a description of how it was obtained. Lattices up to 128^3
+    nodes: one full step, timed. Larger ones (the 512^3 channel: one full step
+    needs ~55 GB of host memory and minutes of CPU time): extrapolated from two
+    timed samples that add up to the step: the lattice update of an
+    nx x ny x nz_s slab of the same lattice (walls and forcing included,
+    nz_s = 2^21 / (nx ny) planes), scaled by nz/nz_s, plus one coupled step of
+    the workload's first chain (one 20,000-bead globule) in a 48^3 box, less
+    that box's own lattice update, times atoms / chain length."""
     import oracle
 
     oracle.build.build_oracle()
-    inp = synth.inputs(cfg, 1)
-    topo = oracle.Topology(inp["mass"], inp["bonds"], inp["bond_k"], inp["bond_r0"])
-    f = oracle.equilibrium(inp["rho"], inp["u"])
-    x, v = inp["x"], inp["v"]
-    if args.warmup:
-        f, x, v, _ = oracle.run(cfg, topo, f, x, v, args.warmup)
-    t0 = time.perf_counter()
-    f, x, v, _ = oracle.run(cfg, topo, f, x, v, args.steps)
-    dt = time.perf_counter() - t0
     nodes = cfg["nx"] * cfg["ny"] * cfg["nz"]
-    val = nodes * args.steps / dt / 1e6
-    sample = f"{args.steps} full coupled steps of {cfg['name']} after {args.warmup} warm-up steps"
+
+    def one_step(c, i):
+        topo = oracle.Topology(i["mass"], i["bonds"], i["bond_k"], i["bond_r0"])
+        f = oracle.equilibrium(i["rho"], i["u"])
+        t0 = time.perf_counter()
+        oracle.run(c, topo, f, i["x"], i["v"], 1)
+        return time.perf_counter() - t0
+
+    if nodes <= 128 ** 3:
+        t = one_step(cfg, inp)
+        return t, f"one full coupled step of {cfg['name']}, timed"
+    nz_slab = max(2, min(cfg["nz"], (1 << 21) // (cfg["nx"] * cfg["ny"])))
+    slab = dict(cfg, nz=nz_slab)
+    t_slab = one_step(slab, synth.inputs(slab, 1, atoms=False))
+    b = inp["bonds"]
+    links = set(b[b[:, 1] == b[:, 0] + 1, 0].tolist())
+    chain = 1  # length of the first chain: beads 0..chain-1 linked by consecutive bonds
+    while chain - 1 in links:
+        chain += 1
+    n_chains = inp["x"].shape[1] / chain
+    sub, sub_inp = _sub_box(cfg, inp, chain)
+    t_glob = one_step(sub, sub_inp)
+    t_sub_lat = one_step(sub, synth.inputs(sub, 1, atoms=False))
+    t = t_slab * cfg["nz"] / nz_slab + n_chains * max(t_glob - t_sub_lat, 0.0)
+    how = (f"extrapolated: lattice update of a {cfg['nx']}x{cfg['ny']}x{nz_slab} slab ({t_slab:.2f} s) x "
+           f"{cfg['nz'] / nz_slab:g}, plus {n_chains:g} x one coupled step of one {chain}-bead globule in a 48^3 box "
+           f"less that box's lattice update ({t_glob:.2f} - {t_sub_lat:.2f} s); one coupled step of the "
+           f"full workload estimated at {t:.1f} s")
+    return t, how
+
+
+def run_reference(args, cfg):
+    """The FP64 oracle on the host cores: each step is one bounded sample of a
+    coupled step of the workload (oracle_step_seconds), single thread."""
+    inp = synth.inputs(cfg, 1)
+    for _ in range(args.warmup):
+        oracle_step_seconds(cfg, inp)
+    times, how = [], ""
+    for _ in range(args.steps):
+        t, how = oracle_step_seconds(cfg, inp)
+        times.append(t)
+    dt = float(np.mean(times))
+    nodes = cfg["nx"] * cfg["ny"] * cfg["nz"]
+    val = nodes / dt / 1e6
+    sample = f"{args.steps} samples after {args.warmup} warm-up, each: {how}"
     return {"impl": "reference", "metric": METRIC, "value": val, "unit": "MLUPS", "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": _config(cfg, inp),
+            "data": "synthetic", "config": _config(cfg, inp, args.stores),
             "cpu_baseline": {"value": val, "unit": "MLUPS", "cores": 1, "kind": "oracle", "sample": sample},
             "e2e": {"value": val, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
-def _config(cfg, inp):
+def _config(cfg, inp, stores):
     na = inp["x"].shape[1]
-    lat = cfg["nx"] * cfg["ny"] * cfg["nz"] * 19 * (4 if cfg["store"] == "f32" else 2) * 2
+    nodes = cfg["nx"] * cfg["ny"] * cfg["nz"]
+    lat = nodes * 19 * (4 if stores[0] == "f32" else 2) * 2
     return {"workload": cfg["name"], "lattice": [cfg["nx"], cfg["ny"], cfg["nz"]], "tau": cfg["tau"],
             "forcing": cfg["forcing"], "force_amp": cfg["force_amp"], "walls_z": cfg["walls_z"],
-            "n_atoms": na, "n_md": cfg["n_md"], "gamma": cfg["gamma"], "store": cfg["store"],
+            "n_atoms": na, "n_md": cfg["n_md"], "gamma": cfg["gamma"], "skin": cfg["skin"],
+            "store": stores[0], "compared_store": stores[1] if len(stores) > 1 else None,
             "l2": f"inputs larger than L2: {lat / 1e6:.0f} MB of populations per step vs 126 MB L2"}
 
 
-def cpu_baseline(cfg, inp, steps=3):
-    """Bounded sample of the oracle on this host: `steps` full coupled steps."""
-    import oracle
-
-    oracle.build.build_oracle()
-    topo = oracle.Topology(inp["mass"], inp["bonds"], inp["bond_k"], inp["bond_r0"])
-    f = oracle.equilibrium(inp["rho"], inp["u"])
-    t0 = time.perf_counter()
-    oracle.run(cfg, topo, f, inp["x"], inp["v"], steps)
-    dt = time.perf_counter() - t0
+def cpu_baseline(cfg, inp):
+    """Bounded sample of the oracle on this host (oracle_step_seconds)."""
+    t, how = oracle_step_seconds(cfg, inp)
     nodes = cfg["nx"] * cfg["ny"] * cfg["nz"]
-    return {"value": nodes * steps / dt / 1e6, "unit": "MLUPS", "cores": 1, "kind": "oracle",
-            "sample": f"{steps} full coupled steps of {cfg['name']} from the initial state, single thread, "
-                      f"{dt:.1f} s"}
+    return {"value": nodes / t / 1e6, "unit": "MLUPS", "cores": 1, "kind": "oracle",
+            "sample": how + ", single thread"}
 
 
 ADJOINT_WORKLOAD = "chain5k_lattice64_uniform"
@@ -247,6 +299,68 @@ def adjoint_timing(stream):
             "adjoint_over_forward": ms / ms_fwd, "mlups_forward_and_adjoint": nodes * steps / (ms * 1e-3) / 1e6}
 
 
+def timed_run(args, cfg, inp, store, local, barrier):
+    """Creates a handle with storage `store`, runs the warm-up steps, then
+    times args.steps coupled steps (one graph launch each) with CUDA events on
+    the caller's stream; the lattice kernel and the chain of substep kernels
+    of every timed step are timed with events recorded by the step graph on
+    their own streams. Returns the handle and the timings."""
+    import torch
+
+    from paper_2305_05025_gb300 import lbmd
+
+    c = dict(cfg, store=store)
+    na = inp["x"].shape[1]
+    h = lbmd.lbmd_create(c, inp["mass"], inp["bonds"], inp["bond_k"], inp["bond_r0"])
+    lbmd.lbmd_set_state(h, rho=inp["rho32"], u=inp["u32"], x=inp["x"], v=inp["v32"])
+    stream = torch.cuda.current_stream()
+    lbmd.lbmd_step(h, args.warmup)
+    lbmd.lbmd_check(h)
+    mk = lambda: (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+    ev_lb = [mk() for _ in range(args.steps)]
+    ev_md = [mk() for _ in range(args.steps)] if na > 0 else []
+    ev_step = [mk() for _ in range(args.steps)]
+    t0, t1 = mk()
+    barrier()
+    with Clocks(local) as clk:
+        t0.record(stream)
+        for i in range(args.steps):
+            # torch only reads events it recorded itself: record each pair here
+            # first; the step graph's record nodes (later, on the library's
+            # streams) set the times that are read.
+            for a, b in [ev_lb[i]] + ([ev_md[i]] if na > 0 else []):
+                a.record(stream)
+                b.record(stream)
+            lbmd.lbmd_set_timing_events(h, ev_lb[i][0], ev_lb[i][1])
+            if na > 0:
+                lbmd.lbmd_set_md_timing_events(h, ev_md[i][0], ev_md[i][1])
+            ev_step[i][0].record(stream)
+            lbmd.lbmd_step(h, 1)
+            ev_step[i][1].record(stream)
+        t1.record(stream)
+        barrier()
+    lbmd.lbmd_set_timing_events(h, None, None)
+    if na > 0:
+        lbmd.lbmd_set_md_timing_events(h, None, None)
+    lbmd.lbmd_check(h)
+    steps_ms = [a.elapsed_time(b) for a, b in ev_step]
+    return h, {"ms": t0.elapsed_time(t1),
+               "lb_ms": float(np.mean([a.elapsed_time(b) for a, b in ev_lb])),
+               "md_ms": float(np.mean([a.elapsed_time(b) for a, b in ev_md])) if na > 0 else 0.0,
+               "step_ms": steps_ms, "clocks": clk.result}
+
+
+def _lattice_roofline(store, nodes, lb_ms, hbm, peak_kind):
+    bpn = 152 if store == "f32" else 76
+    achieved = bpn * nodes / (lb_ms * 1e-3) / 1e9
+    return {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+            "traffic": _traffic(store, nodes),
+            "kernel": f"dense stream-collide ({'k_lb_step' if store == 'f32' else 'k_lb_step_pair16'}<{store}>), "
+                      f"{bpn} B/node algorithmic, {lb_ms * 1e3:.1f} us per launch inside the timed steps "
+                      f"(CUDA events on the lattice stream); peak {peak_kind} copy bandwidth",
+            "mlups": nodes / (lb_ms * 1e-3) / 1e6}
+
+
 def run_ours(args, cfg):
     import torch
 
@@ -259,13 +373,11 @@ def run_ours(args, cfg):
 
         dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
     inp = synth.inputs(cfg, 1 + rank)
+    inp["rho32"], inp["u32"] = inp["rho"].astype(np.float32), inp["u"].astype(np.float32)
+    inp["v32"] = inp["v"].astype(np.float32)
     na = inp["x"].shape[1]
     nodes = cfg["nx"] * cfg["ny"] * cfg["nz"]
-    h = lbmd.lbmd_create(cfg, inp["mass"], inp["bonds"], inp["bond_k"], inp["bond_r0"])
-    rho32, u32 = inp["rho"].astype(np.float32), inp["u"].astype(np.float32)
-    v32 = inp["v"].astype(np.float32)
-    lbmd.lbmd_set_state(h, rho=rho32, u=u32, x=inp["x"], v=v32)
-    stream = torch.cuda.current_stream()
+    n_md = cfg["n_md"]
 
     def barrier():
         torch.cuda.synchronize()
@@ -274,105 +386,111 @@ def run_ours(args, cfg):
 
             dist.barrier()
 
-    lbmd.lbmd_step(h, args.warmup)
-    lbmd.lbmd_check(h)
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    barrier()
-    with Clocks(local) as clk:
-        t0.record(stream)
-        for i in range(args.steps):
-            # torch only reads events it recorded itself: record both here; the
-            # graph's record nodes (later on the same stream) set the times used.
-            ev[i][0].record(stream)
-            ev[i][1].record(stream)
-            lbmd.lbmd_set_timing_events(h, ev[i][0], ev[i][1])
-            lbmd.lbmd_step(h, 1)
-        t1.record(stream)
-        barrier()
-    lbmd.lbmd_set_timing_events(h, None, None)
-    lbmd.lbmd_check(h)
-    ms = t0.elapsed_time(t1)
-    lb_ms = float(np.mean([a.elapsed_time(b) for a, b in ev]))
-    ms, = reduce_max([ms])
+    hbm, peak_kind = _peaks()
+    stores = args.stores
+    runs = {}
+    handle = None
+    for store in stores:
+        h, r = timed_run(args, cfg, inp, store, local, barrier)
+        r["ms"], = reduce_max([r["ms"]])
+        runs[store] = r
+        if store == stores[0]:
+            handle = h
+        else:
+            lbmd.lbmd_destroy(h)
+    prim = runs[stores[0]]
+    ms = prim["ms"]
     value = job_mlups(nodes, args.steps, world, ms * 1e-3)
 
     # End to end through the public API with host buffers: every step copies
-    # the full state in (populations, positions, velocities) from pinned host
-    # memory, advances one step and copies the state out again.
-    e2e_steps = max(3, min(args.steps // 10, 20))
-    st = lbmd.lbmd_get_fields(h, f=True, x=True, v=True)
-    pin = {k: torch.from_numpy(np.ascontiguousarray(a)).pin_memory() for k, a in st.items()}
-    host = {k: t.numpy() for k, t in pin.items()}
-    outs = {k: torch.empty_like(t).pin_memory().numpy() for k, t in pin.items()}
+    # the full state in (FP32 populations, positions, velocities) from pinned
+    # host memory, advances one step and copies the state out again.
+    h = handle
+    e2e_steps = 0 if args.no_e2e else 3
+    pin = {"f": torch.empty((19, nodes), dtype=torch.float32, pin_memory=True),
+           "x": torch.empty((3, na), dtype=torch.float64, pin_memory=True),
+           "v": torch.empty((3, na), dtype=torch.float32, pin_memory=True)}
+    outs = {k: torch.empty_like(t).pin_memory() for k, t in pin.items()}
     import ctypes as C
 
     L = lbmd.lib()
-    vp = lambda a: a.ctypes.data_as(C.c_void_p)
+    vp = lambda t: C.c_void_p(t.data_ptr())
+    assert L.lbmd_get_fields(h, vp(pin["f"]), None, None, vp(pin["x"]), vp(pin["v"]), 0) == 0
     barrier()
     e0 = time.perf_counter()
     for _ in range(e2e_steps):
-        assert L.lbmd_set_state(h, vp(host["f"]), None, None, vp(host["x"]), vp(host["v"]), 0) == 0
+        assert L.lbmd_set_state(h, vp(pin["f"]), None, None, vp(pin["x"]), vp(pin["v"]), 0) == 0
         assert L.lbmd_step(h, 1) == 0
         assert L.lbmd_get_fields(h, vp(outs["f"]), None, None, vp(outs["x"]), vp(outs["v"]), 0) == 0
     barrier()
-    e2e_s = (time.perf_counter() - e0) / e2e_steps
+    e2e_s = (time.perf_counter() - e0) / max(e2e_steps, 1)
     e2e_s, = reduce_max([e2e_s])
-    io_bytes = host["f"].nbytes + host["x"].nbytes + host["v"].nbytes
+    io_bytes = sum(t.numel() * t.element_size() for t in pin.values())
+    lbmd.lbmd_destroy(h)
+    del pin, outs
 
-    hbm, peak_kind = _peaks()
-    bpn = 152 if cfg["store"] == "f32" else 76
-    achieved = bpn * nodes / (lb_ms * 1e-3) / 1e9
-    traffic = _traffic(cfg["store"], nodes)
+    launches = (n_md + 8) if na > 0 else 2  # 3 sort + interp + (n_md + 1) substeps + spread + dense + fix-up
+    lat_roof = {s: _lattice_roofline(s, nodes, runs[s]["lb_ms"], hbm, peak_kind) for s in stores}
     out = {"metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-           "config": _config(cfg, inp),
-           "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                        "frac": achieved / hbm, "traffic": traffic,
-                        "kernel": f"k_lb_step<{cfg['store']}> (dense stream-collide), {bpn} B/node algorithmic, "
-                                  f"{lb_ms * 1e3:.1f} us per launch inside the timed steps; peak {peak_kind}"},
-           "e2e": {"value": job_mlups(nodes, 1, world, e2e_s), "unit": "MLUPS", "h2d_bytes_per_step": io_bytes,
-                   "d2h_bytes_per_step": io_bytes},
-           # per coupled step: 3 sort + interp + (n_md + 1) substeps + spread + dense step + fix-up
-           "gpu_launches": args.steps * ((cfg["n_md"] + 8) if na > 0 else 2),
+           "config": _config(cfg, inp, stores),
+           "roofline": lat_roof[stores[0]],
+           "e2e": ({"value": job_mlups(nodes, 1, world, e2e_s), "unit": "MLUPS", "h2d_bytes_per_step": io_bytes,
+                    "d2h_bytes_per_step": io_bytes} if e2e_steps else None),
+           "gpu_launches": args.steps * launches,
            "atom_updates_per_s": na * args.steps * world / (ms * 1e-3),
-           "lattice_kernel_mlups": nodes / (lb_ms * 1e-3) / 1e6,
-           "clocks": clk.result}
+           "md_substeps_ms_per_step": prim["md_ms"],
+           "md_us_per_substep": prim["md_ms"] * 1e3 / (n_md + 1),
+           "step_ms_min_median_max": [min(prim["step_ms"]), float(np.median(prim["step_ms"])), max(prim["step_ms"])],
+           "clocks": prim["clocks"]}
+    for s in stores[1:]:
+        r = runs[s]
+        out[s] = {"value": job_mlups(nodes, args.steps, world, r["ms"] * 1e-3), "unit": "MLUPS",
+                  "ms_per_step": r["ms"] / args.steps, "lattice": lat_roof[s], "md_substeps_ms_per_step": r["md_ms"],
+                  "step_ms_min_median_max": [min(r["step_ms"]), float(np.median(r["step_ms"])), max(r["step_ms"])],
+                  "clocks": r["clocks"]}
+        out[f"{stores[0]}_over_{s}"] = {"coupled": runs[s]["ms"] / ms,
+                                       "lattice_kernel": runs[s]["lb_ms"] / prim["lb_ms"]}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(cfg, inp)
     if world == 1 and not args.no_adjoint:
-        out["adjoint"] = adjoint_timing(stream)
+        out["adjoint"] = adjoint_timing(torch.cuda.current_stream())
     if world > 1:
         import torch.distributed as dist
 
         dist.destroy_process_group()
-    lbmd.lbmd_destroy(h)
     return out if rank == 0 else None
 
 
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD)
-    ap.add_argument("--store", default="f32", choices=["f32", "f16", "bf16"])
+    ap.add_argument("--store", default="f16,f32",
+                    help="storage formats, comma separated: the first is the headline, the others are timed "
+                         "on the same workload and reported beside it")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true", help="skip the timing of the adjoint workload")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end timing with host buffers")
     args = ap.parse_args()
-    overrides = dict(DEFAULT_OVERRIDES)
-    overrides["store"] = args.store
-    cfg = synth.workload(args.workload, **overrides)
+    args.stores = [s.strip() for s in args.store.split(",") if s.strip()]
+    for s in args.stores:
+        if s not in ("f32", "f16", "bf16"):
+            ap.error(f"unknown store {s}")
+    cfg = synth.workload(args.workload, **DEFAULT_OVERRIDES)
+    cfg["store"] = args.stores[0]
     if args.impl == "reference":
         world, rank, _ = _dist()
         if rank != 0:
             return
-        # Each oracle step of the 128^3 workload takes ~10 s on one core: at
-        # most 10 timed steps after at most 1 warm-up keep the run near two
-        # minutes (the line reports the steps actually taken).
-        args.steps = min(args.steps, 10)
+        # Each oracle sample takes ~10-30 s on one core: at most 5 timed
+        # samples after at most 1 warm-up keep the run within a few minutes
+        # (the line reports the samples actually taken).
+        args.steps = min(args.steps, 5)
         args.warmup = min(args.warmup, 1)
         out = run_reference(args, cfg)
     else:

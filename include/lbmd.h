@@ -102,8 +102,12 @@ typedef struct {
                                  many steps (0: only lbmd_check / lbmd_get_stats do) */
 } lbmd_params;
 
-/* Creates a handle: validates the parameters (LBMD_ERR_ARG before any device
- * work), allocates the lattice (two population buffers of N*19 elements of
+/* Creates a handle. Passage: Sec. 2.2 -- the lattice of Eq. (1) (nx, ny, nz
+ * nodes, D3Q19), its relaxation omega = 1/tau with nu = (tau - 1/2)/3, the
+ * friction coefficient gamma of the atom-fluid coupling, and the solute
+ * (masses, bonded topology, the Lennard-Jones short-range force field that
+ * stands in for the paper's force field). Validates the parameters
+ * (LBMD_ERR_ARG before any device work), allocates the lattice (two population buffers of N*19 elements of
  * the storage format), the atom arrays and the pair-search cells, and uploads
  * the topology. mass: n_atoms masses (> 0). bonds: 2*n_bonds atom indices;
  * bond_k, bond_r0: n_bonds stiffnesses and rest lengths (U = k (r - r0)^2/2).
@@ -114,7 +118,8 @@ lbmd_status lbmd_create(const lbmd_params *params, int n_atoms, const double *ma
                         const int32_t *bonds, const double *bond_k, const double *bond_r0,
                         void *cuda_stream, lbmd_t *out);
 
-/* Sets the state. f: FP32 post-streaming populations (19*N SoA); or, when f
+/* Sets the state (Sec. 2.2: the populations f_i(r, t) of Eq. (1) and the
+ * atom positions and velocities). f: FP32 post-streaming populations (19*N SoA); or, when f
  * is NULL, rho (N) and u (3*N SoA) give f = f_eq(rho, u) (the second-order
  * equilibrium of Sec. 2.2). x (FP64) and v (FP32): 3*n_atoms SoA, required
  * when n_atoms > 0. Also computes the conservative forces at x and fills
@@ -122,28 +127,37 @@ lbmd_status lbmd_create(const lbmd_params *params, int n_atoms, const double *ma
 lbmd_status lbmd_set_state(lbmd_t h, const float *f, const float *rho, const float *u,
                            const double *x, const float *v, int on_device);
 
-/* Advances n_steps coupled steps (asynchronous; each step is one CUDA graph
- * launch). Returns LBMD_ERR_STATE if no state was set. Polls the device flags
+/* Advances n_steps coupled steps (Sec. 2.2, Eq. 1: one lattice-Boltzmann
+ * update per step in lock step with the MD, which takes n_md velocity-Verlet
+ * substeps; the friction gamma (u - v) couples them through trilinear
+ * interpolation over the eight nearest nodes and the equal and opposite
+ * source term). Asynchronous; each step is one CUDA graph launch. Returns LBMD_ERR_STATE if no state was set. Polls the device flags
  * only when check_every > 0 and a multiple of it is crossed. */
 lbmd_status lbmd_step(lbmd_t h, int n_steps);
 
-/* Copies out the current state; any pointer may be NULL. f: FP32
- * post-streaming populations (19*N); rho (N); u (3*N), the velocity
+/* Copies out the current state (Sec. 2.2; rho and u are the moments of
+ * Eq. 2); any pointer may be NULL. f: FP32 post-streaming populations (19*N); rho (N); u (3*N), the velocity
  * (sum f c + g/2)/rho; x (3*n_atoms FP64); v (3*n_atoms FP32). Synchronises
  * the stream when on_device = 0. */
 lbmd_status lbmd_get_fields(lbmd_t h, float *f, float *rho, float *u, double *x, float *v,
                             int on_device);
 
-/* FP64 global sums: fluid mass sum_x sum_i f_i, fluid momentum
+/* Conservation diagnostics (Sec. 2.2: the source term of Eq. (1) keeps mass
+ * and momentum, and the fluid receives exactly the impulse the atoms lose, so
+ * mass is constant and total momentum grows by sum_x g per step). FP64 global
+ * sums: fluid mass sum_x sum_i f_i, fluid momentum
  * sum_x sum_i f_i c_i, solute momentum sum_a m_a v_a (host outputs, any may be
  * NULL). Synchronises; returns LBMD_ERR_NONFINITE if a NaN/Inf was found. */
 lbmd_status lbmd_get_stats(lbmd_t h, double *mass, double mom_fluid[3], double mom_atoms[3]);
 
-/* Synchronises and returns the first raised device flag as a status
+/* Error poll (no counterpart in the paper: a service of this library).
+ * Synchronises and returns the first raised device flag as a status
  * (NONFINITE, CELL, STATE), clearing the flags. */
 lbmd_status lbmd_check(lbmd_t h);
 
-/* Pair-search diagnostics at the current positions: cell_of[a] = linear
+/* Pair-search diagnostics (the cell list of the short-range forces; the
+ * paper's MD engine keeps one internally, Sec. 2.2, and states no layout):
+ * cell_of[a] = linear
  * index (cz*ncy + cy)*ncx + cx of atom a's cell, cx = floor(x*ncx/nx) mod ncx
  * in FP64, ncx = floor(nx/(rcut + skin)); neighbours[a] = number of other
  * atoms with r^2 < rcut^2 (FP64, minimum image). nc (3 ints, host) receives
@@ -152,16 +166,41 @@ lbmd_status lbmd_cell_list(lbmd_t h, int32_t *cell_of, int32_t *neighbours, int3
                            int on_device);
 
 /* Changes gamma, tau and the body-force amplitude of an existing handle
- * (the step graph is rebuilt on the next lbmd_step). */
+ * (Sec. 2.2: the coupling and relaxation parameters the adjoint
+ * differentiates); the step graph is rebuilt on the next lbmd_step. */
 lbmd_status lbmd_set_physics(lbmd_t h, double gamma, double tau, double force_amp);
 
-/* Routes the start/stop of the lattice kernel of the NEXT step launch to two
+/* Thermal fluctuations of the fluid (Sec. 2.2: the noise xi_i of the
+ * fluctuating lattice Boltzmann source term S_i = p_i + xi_i of Eq. 1, the
+ * fluid acting as the heat bath). kT > 0 adds after every collision, at every
+ * node, Gaussian noise on the 15 non-conserved modes of the D3Q19 moment
+ * basis with variance mu b_k (1 - (1 - omega)^2), mu = rho0 kT / c_s^2, so
+ * that at rest each node's density fluctuates with variance rho0 kT / c_s^2
+ * and each momentum component with rho0 kT; mass and momentum are exact.
+ * kT = 0 (the default) turns it off. The random numbers are Philox4x32-10
+ * with counter (node, block, step) and key `seed`: a run is reproducible for
+ * a given seed and state, and the step counter restarts at lbmd_set_state.
+ * The step graph is rebuilt on the next lbmd_step. lbmd_backward refuses
+ * kT > 0 (LBMD_ERR_ARG). */
+lbmd_status lbmd_set_thermal(lbmd_t h, double kT, uint64_t seed);
+
+/* Timing hook (no counterpart in the paper). Routes the start/stop of the
+ * lattice kernel of the NEXT step launch to two
  * caller events (cudaEvent_t, created with timing enabled), so the caller can
  * time that kernel with cudaEventElapsedTime on the stream it runs on.
  * NULL, NULL restores the library's own events. */
 lbmd_status lbmd_set_timing_events(lbmd_t h, void *ev_start, void *ev_stop);
 
-/* Differentiable rollout (not in the paper: the adjoint of the coupled step).
+/* Timing hook (no counterpart in the paper). Like lbmd_set_timing_events,
+ * for the chain of the n_md + 1 velocity-Verlet
+ * substep kernels of each step (on the library's solute stream): ev_start is
+ * recorded before the first substep kernel, ev_stop after the last. Returns
+ * LBMD_ERR_ARG for a lattice-only handle (n_atoms = 0). */
+lbmd_status lbmd_set_md_timing_events(lbmd_t h, void *ev_start, void *ev_stop);
+
+/* Differentiable rollout (not in the paper: the discrete adjoint of the
+ * coupled step of Sec. 2.2, Eq. 1, for calibrating its gamma, tau and
+ * forcing).
  * Runs n_steps steps from the current state, keeping a checkpoint every
  * ckpt_every steps, evaluates the observable (LBMD_OBS_*) and, by the
  * discrete adjoint (reverse collide-stream, reverse interpolate/spread,
@@ -171,14 +210,49 @@ lbmd_status lbmd_set_timing_events(lbmd_t h, void *ev_start, void *ev_stop);
 lbmd_status lbmd_backward(lbmd_t h, int n_steps, int ckpt_every, int observable, double *d_gamma,
                           double *d_tau, double *d_force_amp, double *obs);
 
-/* Message of the last failed call on this handle (or of the last failed
+/* Trajectory analysis of the solute (the analyses of Sec. 3 of the paper:
+ * root-mean-square deviation from the starting structure, radius of
+ * gyration, per-atom root-mean-square fluctuation and the principal
+ * components of the atomic fluctuations), computed on the device.
+ *
+ * lbmd_analysis_begin selects n_sel atoms (sel: host array of atom indices;
+ * NULL: all atoms, n_sel ignored) and a reference structure x_ref (host,
+ * 3*n_sel FP64 SoA; NULL: the selected atoms' current positions), and
+ * reserves device storage for max_frames frames (3*n_sel FP32 each); it
+ * replaces any earlier analysis of the handle. LBMD_ERR_ARG for an empty or
+ * out-of-range selection, a non-finite reference or more than 64 GB of
+ * frames. Synchronises the stream. */
+lbmd_status lbmd_analysis_begin(lbmd_t h, int n_sel, const int32_t *sel, const double *x_ref, int max_frames);
+
+/* Takes one frame at the current positions. rg2 (host, may be NULL): the
+ * mass-weighted squared radius of gyration of all atoms. rmsd (host, may be
+ * NULL): the root-mean-square deviation of the selection from the reference
+ * after the optimal rigid superposition (unweighted least squares, proper
+ * rotation plus translation). The superposed displacements from the reference
+ * are stored as frame number k (k = frames taken so far). FP64 sums on the
+ * device, the 4x4 eigenproblem of the optimal rotation on the host.
+ * Synchronises the stream. LBMD_ERR_ARG once max_frames frames are taken,
+ * LBMD_ERR_STATE before lbmd_analysis_begin. */
+lbmd_status lbmd_analysis_frame(lbmd_t h, double *rg2, double *rmsd);
+
+/* Over the T frames taken: mean_disp (3*n_sel FP64 SoA), the mean superposed
+ * displacement from the reference; rmsf (n_sel FP64), sqrt of the mean over
+ * frames of |d_t - mean|^2 per atom; cov ((3 n_sel)^2 FP32, row-major,
+ * coordinate index d*n_sel + i), the covariance (1/T) sum_t (d_t - mean)
+ * (d_t - mean)^T whose eigenvectors are the principal components. Any output
+ * may be NULL; on_device as elsewhere. The frames stay: more may be taken and
+ * the result asked again. LBMD_ERR_STATE before the first frame. */
+lbmd_status lbmd_analysis_result(lbmd_t h, double *mean_disp, double *rmsf, float *cov, int on_device);
+
+/* (No counterpart in the paper.) Message of the last failed call on this handle (or of the last failed
  * lbmd_create on this thread when h is NULL). Never NULL. */
 const char *lbmd_last_error(lbmd_t h);
 
-/* Frees every resource of the handle (synchronises its stream). NULL is a no-op. */
+/* (No counterpart in the paper.) Frees every resource of the handle
+ * (synchronises its stream). NULL is a no-op. */
 void lbmd_destroy(lbmd_t h);
 
-/* ABI version, currently 1. */
+/* (No counterpart in the paper.) ABI version, currently 1. */
 int lbmd_version(void);
 
 /* Largest lattice lbmd_fluid_sums_noalloc accepts: 65536 blocks of 256 nodes

@@ -9,6 +9,8 @@
 // other. One thread per node, threads along x within a warp, so each of the 19
 // loads and stores of a warp is one contiguous run (shifted by one element for
 // speeds with c_x != 0).
+#include <algorithm>
+
 #include "lbmd_internal.cuh"
 
 namespace lbmd {
@@ -37,7 +39,7 @@ __device__ __forceinline__ void pull_node(const typename Store<S>::T *sp, ptrdif
 // i starts at i * plane_bytes, and the collision pairs each speed with its
 // opposite and is specialised on the direction FD of the body force
 // (collide_g), in stored units.
-template <int S, int FD>
+template <int S, int FD, bool TH>
 __global__ void __launch_bounds__(256) k_lb_step(Lat L, typename Store<S>::T *b0, typename Store<S>::T *b1,
                                                  DevState *ds) {
     using T = typename Store<S>::T;
@@ -65,6 +67,12 @@ __global__ void __launch_bounds__(256) k_lb_step(Lat L, typename Store<S>::T *b0
         pull_node<S, false>(src + node, plane, oxm, oxp, oym, oyp, ozm, ozp, false, false, f);
     const float rho = collide_g<FD, Store<S>::kScaled>(L, f, body_amp(L, x, y, z));
     if (!isfinite(rho)) atomicOr(&ds->flags, FLAG_NONFINITE);
+    if (TH) {  // thermal noise, in stored units
+        float xi[Q];
+        node_noise(L, (unsigned)node, (unsigned)step, Store<S>::kScaled ? kF16Scale : 1.f, xi);
+#pragma unroll
+        for (int i = 0; i < Q; ++i) f[i] += xi[i];
+    }
     T *dp = dst + node;
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
@@ -136,7 +144,7 @@ __device__ __forceinline__ void pull_pair(const typename Store<S>::T *sp, ptrdif
 // packed until used), the +-1 shift of the pull along x is assembled from the
 // neighbouring lane's word (or one 16-bit load at a row or warp edge), and
 // both results leave as one 32-bit store.
-template <int S, int FD>
+template <int S, int FD, bool TH>
 __global__ void __launch_bounds__(128, 7) k_lb_step_pair16(Lat L, typename Store<S>::T *b0, typename Store<S>::T *b1,
                                                         DevState *ds) {
     using T = typename Store<S>::T;
@@ -180,9 +188,180 @@ __global__ void __launch_bounds__(128, 7) k_lb_step_pair16(Lat L, typename Store
     for (int i = 0; i < Q; ++i) fab[i] = H::unpack(w[i]);
     const float2 r = collide_g2<FD, Store<S>::kScaled>(L, fab, ga);
     if (!isfinite(r.x) || !isfinite(r.y)) atomicOr(&ds->flags, FLAG_NONFINITE);
+    if (TH) {  // thermal noise of both nodes, in stored units
+        const float sc = Store<S>::kScaled ? kF16Scale : 1.f;
+        float xi[Q];
+        node_noise(L, (unsigned)node, (unsigned)step, sc, xi);
+#pragma unroll
+        for (int i = 0; i < Q; ++i) fab[i].x += xi[i];
+        node_noise(L, (unsigned)node + 1u, (unsigned)step, sc, xi);
+#pragma unroll
+        for (int i = 0; i < Q; ++i) fab[i].y += xi[i];
+    }
     T *dp = dst + node;
 #pragma unroll
     for (int i = 0; i < Q; ++i, dp += plane) __stcs(reinterpret_cast<unsigned *>(dp), H::pack(fab[i].x, fab[i].y));
+}
+
+// ---------------------------------------------------------------------------
+// 16-bit storage, whole rows through shared memory. A persistent block walks
+// lattice rows (y, z); for each row one elected thread issues 19 bulk copies
+// (cp.async.bulk, completion counted on an mbarrier), one per population:
+// the whole source row the pull needs, (y - c_y, z - c_z), or the node's own
+// row of the opposite population where the pull would cross a z wall. Rows
+// are double-buffered, so the next row's 19 copies are in flight while this
+// one is collided. The x shift of the pull is then a shared-memory read
+// (periodic in x within the row) and a byte permute; each thread collides
+// node pairs (x0, x0 + 1) in packed FP32x2 as in k_lb_step_pair16 and
+// stores them with 32-bit streaming stores. Every wait on an mbarrier is
+// bounded (about a second): on expiry the block raises FLAG_TIMEOUT, waits
+// (bounded again) for its copies still in flight, and returns.
+
+__device__ __forceinline__ unsigned smem_addr(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(unsigned long long *bar, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long *bar, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ void bulk_copy_g2s(void *dst, const void *src, unsigned bytes, unsigned long long *bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_addr(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_addr(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_test(unsigned long long *bar, unsigned parity) {
+    unsigned done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(done)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return done != 0;
+}
+
+// Waits for phase `parity` of the barrier for at most ~2^31 clock cycles
+// (about a second at 2 GHz); false on expiry.
+__device__ __forceinline__ bool mbar_wait_bounded(unsigned long long *bar, unsigned parity) {
+    const long long t0 = clock64();
+    while (!mbar_test(bar, parity))
+        if (clock64() - t0 > (1ll << 31)) return false;
+    return true;
+}
+
+constexpr int kRowThreads = 128;
+
+template <int S, int FD, bool TH>
+__global__ void __launch_bounds__(kRowThreads, 5) k_lb_step_rows16(Lat L, typename Store<S>::T *b0,
+                                                                 typename Store<S>::T *b1, DevState *ds) {
+    using T = typename Store<S>::T;
+    using H = Half16<S>;
+    extern __shared__ __align__(128) unsigned char s_rows[];  // [2][Q][nx] 16-bit values
+    __shared__ unsigned long long s_bar[2];
+    __shared__ int s_fail;
+    const int nx = L.nx, ny = L.ny, nz = L.nz, nxy = nx * ny;
+    const int nrows = ny * nz, half = nx / 2;
+    const unsigned row_bytes = (unsigned)nx * 2u;
+    const int step = ds->step;
+    const T *src = (step & 1) ? b1 : b0;
+    T *dst = (step & 1) ? b0 : b1;
+    const size_t plane = L.N;
+    auto stage = [&](int st, int i) { return reinterpret_cast<const unsigned *>(s_rows + ((size_t)st * Q + i) * row_bytes); };
+    // Copies of row r (y = r % ny, z = r / ny) into stage st, by one thread.
+    auto issue = [&](int r, int st) {
+        const int y = r % ny, z = r / ny;
+        mbar_expect_tx(&s_bar[st], Q * row_bytes);
+#pragma unroll 1
+        for (int i = 0; i < Q; ++i) {
+            const bool wall = L.walls && ((cz(i) == 1 && z == 0) || (cz(i) == -1 && z == nz - 1));
+            int q = i, ys = y, zs = z;
+            if (wall) {
+                q = opp(i);
+            } else {
+                ys = y - cy(i);
+                ys += ys < 0 ? ny : (ys >= ny ? -ny : 0);
+                zs = z - cz(i);
+                zs += zs < 0 ? nz : (zs >= nz ? -nz : 0);
+            }
+            const T *g = src + (size_t)q * plane + ((size_t)zs * ny + ys) * nx;
+            bulk_copy_g2s(s_rows + ((size_t)st * Q + i) * row_bytes, g, row_bytes, &s_bar[st]);
+        }
+    };
+    if (threadIdx.x == 0) {
+        mbar_init(&s_bar[0], 1);
+        mbar_init(&s_bar[1], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        s_fail = 0;
+        if ((int)blockIdx.x < nrows) issue(blockIdx.x, 0);
+        if ((int)(blockIdx.x + gridDim.x) < nrows) issue(blockIdx.x + gridDim.x, 1);
+    }
+    __syncthreads();
+    int k = 0;
+    for (int r = blockIdx.x; r < nrows; r += gridDim.x, ++k) {
+        const int st = k & 1;
+        const unsigned parity = (unsigned)(k >> 1) & 1u;
+        if (!mbar_wait_bounded(&s_bar[st], parity)) s_fail = 1;
+        __syncthreads();
+        if (s_fail) break;
+        const int y = r % ny, z = r / ny;
+        const float ga = body_amp(L, 0, y, z);
+        for (int p = threadIdx.x; p < half; p += kRowThreads) {
+            float2 fab[Q];
+#pragma unroll
+            for (int i = 0; i < Q; ++i) {
+                const bool wall = L.walls && ((cz(i) == 1 && z == 0) || (cz(i) == -1 && z == nz - 1));
+                const unsigned *row = stage(st, i);
+                unsigned w;
+                if (cx(i) == 0 || wall) {
+                    w = row[p];
+                } else if (cx(i) == 1) {  // nodes x0, x0 + 1 pull x0 - 1, x0
+                    w = __byte_perm(row[p == 0 ? half - 1 : p - 1], row[p], 0x5432);
+                } else {  // nodes x0, x0 + 1 pull x0 + 1, x0 + 2
+                    w = __byte_perm(row[p], row[p + 1 == half ? 0 : p + 1], 0x5432);
+                }
+                fab[i] = H::unpack(w);
+            }
+            const float2 rr = collide_g2<FD, Store<S>::kScaled>(L, fab, ga);
+            if (!isfinite(rr.x) || !isfinite(rr.y)) atomicOr(&ds->flags, FLAG_NONFINITE);
+            const int node = z * nxy + y * nx + 2 * p;
+            if (TH) {
+                const float sc = Store<S>::kScaled ? kF16Scale : 1.f;
+                float xi[Q];
+                node_noise(L, (unsigned)node, (unsigned)step, sc, xi);
+#pragma unroll
+                for (int i = 0; i < Q; ++i) fab[i].x += xi[i];
+                node_noise(L, (unsigned)node + 1u, (unsigned)step, sc, xi);
+#pragma unroll
+                for (int i = 0; i < Q; ++i) fab[i].y += xi[i];
+            }
+            T *dp = dst + node;
+#pragma unroll
+            for (int i = 0; i < Q; ++i, dp += plane)
+                __stcs(reinterpret_cast<unsigned *>(dp), H::pack(fab[i].x, fab[i].y));
+        }
+        __syncthreads();  // stage st is read: refill it with the row after next
+        if (threadIdx.x == 0 && r + 2 * (int)gridDim.x < nrows) {
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // reads above before the copies' writes
+            issue(r + 2 * gridDim.x, st);
+        }
+    }
+    if (s_fail) {
+        // Let the copies still in flight land before the block's shared
+        // memory goes away (bounded again), and report.
+        if (threadIdx.x == 0) {
+            atomicOr(&ds->flags, FLAG_TIMEOUT);
+            for (int j = k; j < k + 2; ++j) {
+                const int r = blockIdx.x + j * gridDim.x;
+                if (r < nrows) mbar_wait_bounded(&s_bar[j & 1], (unsigned)(j >> 1) & 1u);
+            }
+        }
+        __syncthreads();
+    }
 }
 
 // Nodes touched by atoms: redo the collision with F = g + G from the same
@@ -210,6 +389,12 @@ __global__ void __launch_bounds__(256) k_lb_fix(Lat L, typename Store<S>::T *b0,
         F[2] += Gn.z;
         const float rho = collide(L, f, F);
         if (!isfinite(rho)) atomicOr(&ds->flags, FLAG_NONFINITE);
+        if (L.thermal) {  // the same noise the dense kernel added at this node and step
+            float xi[Q];
+            node_noise(L, (unsigned)node, (unsigned)step, 1.f, xi);
+#pragma unroll
+            for (int q = 0; q < Q; ++q) f[q] += xi[q];
+        }
 #pragma unroll
         for (int q = 0; q < Q; ++q) Store<S>::st_plain(dst + (size_t)q * L.N + node, f[q]);
         if (!keep) G[node] = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -406,16 +591,61 @@ dim3 node_grid(const Lat &L, dim3 b) { return dim3((L.nx + b.x - 1) / b.x, (L.ny
     }
 
 // Runs BODY with FDV bound at compile time to the body-force direction
-// (-1 without forcing).
-#define LBMD_FD_DISPATCH(L, BODY)                                          \
+// (-1 without forcing) and THV to the thermal-noise switch.
+#define LBMD_FD_DISPATCH1(L, BODY)                                         \
     switch ((L).forcing == LBMD_FORCE_NONE ? -1 : (L).fdir) {             \
         case -1: { constexpr int FDV = -1; BODY; } break;                  \
         case 0: { constexpr int FDV = 0; BODY; } break;                    \
         case 1: { constexpr int FDV = 1; BODY; } break;                    \
         default: { constexpr int FDV = 2; BODY; } break;                   \
     }
+#define LBMD_FD_DISPATCH(L, BODY)                                          \
+    if ((L).thermal) {                                                     \
+        constexpr bool THV = true;                                         \
+        LBMD_FD_DISPATCH1(L, BODY)                                         \
+    } else {                                                               \
+        constexpr bool THV = false;                                        \
+        LBMD_FD_DISPATCH1(L, BODY)                                         \
+    }
+
+// Shared memory of the row kernel: two stages of 19 rows of nx 16-bit values.
+size_t rows16_smem(const Lat &L) { return (size_t)2 * Q * L.nx * 2; }
+
+// Row kernel for 16-bit storage: rows of whole 16-byte multiples (nx % 8 = 0)
+// that fit two stages in shared memory, body force uniform along x.
+bool use_rows16(int store, const Lat &L) {
+    return store != LBMD_F32 && L.nx % 8 == 0 && rows16_smem(L) <= 200 * 1024 &&
+           !(L.forcing == LBMD_FORCE_KOLMOGOROV && L.faxis == 0);
+}
+
+template <int SV, int FDV, bool THV>
+cudaError_t launch_rows16(const Lat &L, void *const buf[2], DevState *ds, cudaStream_t s) {
+    using T = typename Store<SV>::T;
+    const size_t smem = rows16_smem(L);
+    auto kern = k_lb_step_rows16<SV, FDV, THV>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    int per_sm = 0, dev = 0, sms = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kRowThreads, smem);
+    if (e != cudaSuccess) return e;
+    e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    const long long rows = (long long)L.ny * L.nz;
+    const int grid = (int)std::min<long long>(rows, (long long)std::max(per_sm, 1) * sms);
+    kern<<<grid, kRowThreads, smem, s>>>(L, (T *)buf[0], (T *)buf[1], ds);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_lb_step(int store, const Lat &L, void *const buf[2], DevState *ds, cudaStream_t s) {
+    if (use_rows16(store, L)) {
+        if (store == LBMD_F16_SHIFTED) {
+            LBMD_FD_DISPATCH(L, return (launch_rows16<LBMD_F16_SHIFTED, FDV, THV>(L, buf, ds, s)));
+        } else {
+            LBMD_FD_DISPATCH(L, return (launch_rows16<LBMD_BF16_SHIFTED, FDV, THV>(L, buf, ds, s)));
+        }
+    }
     const bool pairs = store != LBMD_F32 && L.nx % 2 == 0 &&
                        !(L.forcing == LBMD_FORCE_KOLMOGOROV && L.faxis == 0);
     if (pairs) {
@@ -426,16 +656,16 @@ cudaError_t launch_lb_step(int store, const Lat &L, void *const buf[2], DevState
         if (by > L.ny) by = L.ny;
         const dim3 b(bx, by, 1), g((half + bx - 1) / bx, (L.ny + by - 1) / by, L.nz);
         if (store == LBMD_F16_SHIFTED) {
-            LBMD_FD_DISPATCH(L, (k_lb_step_pair16<LBMD_F16_SHIFTED, FDV>
+            LBMD_FD_DISPATCH(L, (k_lb_step_pair16<LBMD_F16_SHIFTED, FDV, THV>
                                  <<<g, b, 0, s>>>(L, (__half *)buf[0], (__half *)buf[1], ds)));
         } else {
-            LBMD_FD_DISPATCH(L, (k_lb_step_pair16<LBMD_BF16_SHIFTED, FDV>
+            LBMD_FD_DISPATCH(L, (k_lb_step_pair16<LBMD_BF16_SHIFTED, FDV, THV>
                                  <<<g, b, 0, s>>>(L, (__nv_bfloat16 *)buf[0], (__nv_bfloat16 *)buf[1], ds)));
         }
         return cudaGetLastError();
     }
     const dim3 b = node_block(L), g = node_grid(L, b);
-    LBMD_FD_DISPATCH(L, LBMD_DISPATCH(store, (k_lb_step<SV, FDV><<<g, b, 0, s>>>(L, (T *)buf[0], (T *)buf[1], ds))));
+    LBMD_FD_DISPATCH(L, LBMD_DISPATCH(store, (k_lb_step<SV, FDV, THV><<<g, b, 0, s>>>(L, (T *)buf[0], (T *)buf[1], ds))));
     return cudaGetLastError();
 }
 

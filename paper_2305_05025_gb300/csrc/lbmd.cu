@@ -4,11 +4,12 @@
 //
 // One coupled step is one graph launch with two branches:
 //   lattice branch (low priority):  dense stream-collide of every node (g only)
-//   solute branch (high priority):  interpolate + claim -> n_md+1 substep
-//                                   kernels -> spread
+//   solute branch (high priority):  sort + interpolate + claim -> n_md+1
+//                                   substep kernels -> spread
 // joined by the sparse fix-up of the claimed nodes (g + G), whose last block
 // advances the device step counter. The dense lattice pass does not depend on
 // the solute, so the two branches overlap.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
@@ -40,9 +41,12 @@ void lbmd::set_thread_error(const std::string &msg) { g_create_error = msg; }
 
 struct lbmd_s {
     lbmd_params p{};
+    double kT = 0.0;          // thermal noise (lbmd_set_thermal)
+    uint64_t seed = 0;
     cudaStream_t stream = nullptr;            // caller's stream
     cudaStream_t s_main = nullptr, s_lat = nullptr;
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_t0 = nullptr, ev_t1 = nullptr;
+    cudaEvent_t ev_m0 = nullptr, ev_m1 = nullptr;  // bracket the n_md + 1 substep kernels
     int na = 0, nb = 0;
     Lat L{};
     AtomArgs A{};
@@ -56,7 +60,7 @@ struct lbmd_s {
     std::vector<void *> allocs;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
-    cudaGraphNode_t node_t0 = nullptr, node_t1 = nullptr;
+    cudaGraphNode_t node_t0 = nullptr, node_t1 = nullptr, node_m0 = nullptr, node_m1 = nullptr;
     bool state_set = false;
     long long steps = 0;
     std::string err;
@@ -77,6 +81,12 @@ struct lbmd_s {
     int *adj_count = nullptr, *adj_slot = nullptr;
     double *obs_acc = nullptr;  // [0] sum, [1..7] scratch
     int adj_blocks = 0;
+    // trajectory analysis (lbmd_analysis_*), allocated by lbmd_analysis_begin
+    std::vector<void *> ana_allocs;
+    AnaArgs ana{};
+    double ana_ybar[3] = {0, 0, 0}, ana_ey = 0.0;
+    int ana_frames = 0, ana_max = 0;
+    float *ana_cov = nullptr;  // device covariance for host outputs (lazily)
 };
 
 namespace {
@@ -192,6 +202,22 @@ void fill_physics(lbmd_t h) {
     L.famp = (float)p.force_amp;
     L.fdir = p.force_dir;
     L.faxis = p.force_wave_axis;
+    // Thermal noise amplitudes a_k = sqrt(mu (1 - (1 - omega)^2) / b_k),
+    // mu = rho0 kT / c_s^2, b_k = sum_i w_i e_k(c_i)^2, in FP64.
+    L.thermal = h->kT > 0.0;
+    L.key0 = (unsigned)(h->seed & 0xffffffffu);
+    L.key1 = (unsigned)(h->seed >> 32);
+    {
+        const double om = 1.0 / p.tau, g = 1.0 - om, mu = 3.0 * p.rho0 * h->kT;
+        for (int k = 4; k < Q; ++k) {
+            double b = 0.0;
+            for (int i = 0; i < Q; ++i) {
+                const double wi = i == 0 ? 1.0 / 3.0 : (i <= 6 ? 1.0 / 18.0 : 1.0 / 36.0);
+                b += wi * (double)emode(k, i) * (double)emode(k, i);
+            }
+            L.namp[k - 4] = (float)std::sqrt(mu * (1.0 - g * g) / b);
+        }
+    }
 
     AtomArgs &A = h->A;
     A.na = h->na;
@@ -247,7 +273,7 @@ void destroy_graph(lbmd_t h) {
     if (h->graph) cudaGraphDestroy(h->graph);
     h->exec = nullptr;
     h->graph = nullptr;
-    h->node_t0 = h->node_t1 = nullptr;
+    h->node_t0 = h->node_t1 = h->node_m0 = h->node_m1 = nullptr;
 }
 
 lbmd_status enqueue_step(lbmd_t h) {
@@ -258,11 +284,14 @@ lbmd_status enqueue_step(lbmd_t h) {
     CK(h, launch_lb_step(h->p.store, h->L, h->pop, h->ds, h->s_lat));
     CK(h, cudaEventRecordWithFlags(h->ev_t1, h->s_lat, cudaEventRecordExternal));
     CK(h, cudaEventRecord(h->ev_join, h->s_lat));
-    // Solute branch.
+    // Solute branch, beside the lattice branch (at 512^3 a schedule that
+    // waited for the lattice kernel before the substeps measured the same).
     if (h->na > 0) {
         CK(h, launch_md_sort(h->A, h->s_main));
         CK(h, launch_interp(h->p.store, h->C, h->A, h->pop, h->s_main));
+        CK(h, cudaEventRecordWithFlags(h->ev_m0, h->s_main, cudaEventRecordExternal));
         for (int k = 0; k <= h->A.n_md; ++k) CK(h, launch_md_substep(h->A, k, h->s_main));
+        CK(h, cudaEventRecordWithFlags(h->ev_m1, h->s_main, cudaEventRecordExternal));
         CK(h, launch_spread(h->C, h->s_main));
     }
     CK(h, cudaStreamWaitEvent(h->s_main, h->ev_join, 0));
@@ -295,6 +324,8 @@ lbmd_status build_graph(lbmd_t h) {
         CK(h, cudaGraphEventRecordNodeGetEvent(nd, &ev));
         if (ev == h->ev_t0) h->node_t0 = nd;
         if (ev == h->ev_t1) h->node_t1 = nd;
+        if (ev == h->ev_m0) h->node_m0 = nd;
+        if (ev == h->ev_m1) h->node_m1 = nd;
     }
     return LBMD_OK;
 }
@@ -310,6 +341,8 @@ lbmd_status read_flags(lbmd_t h) {
     if (flags & FLAG_NONFINITE) return fail(h, LBMD_ERR_NONFINITE, "non-finite value in the lattice or the atoms");
     if (flags & FLAG_CELL)
         return fail(h, LBMD_ERR_CELL, "a pair-search bucket overflowed: forces of a step missed pairs");
+    if (flags & FLAG_TIMEOUT)
+        return fail(h, LBMD_ERR_CUDA, "a lattice kernel gave up waiting for its bulk copies (bounded wait expired)");
     if (flags & FLAG_WALL) return fail(h, LBMD_ERR_STATE, "an atom's interpolation stencil crossed a z wall");
     return fail(h, LBMD_ERR_STATE, "touched-node list overflowed");
 }
@@ -460,6 +493,86 @@ lbmd_status enqueue_record_step(lbmd_t h) {
     return LBMD_OK;
 }
 
+// Optimal superposition (Horn's quaternion form of the least-squares rotation,
+// J. Opt. Soc. Am. A 4, 629 (1987)): for centred coordinate sets x and y with
+// S[a][b] = sum_i x_ia y_ib, the rotation R maximising sum_i y_i . R x_i is
+// given by the unit quaternion of the largest eigenvalue lambda of the
+// symmetric 4x4 matrix N(S) below, and that maximum is lambda, so the
+// least-squares residual is |x|^2 + |y|^2 - 2 lambda. Eigenpairs by cyclic
+// Jacobi rotations in FP64. Returns lambda; R is row-major, y ~ R x.
+double horn_rotation(const double S[9], double R[9]) {
+    const double Sxx = S[0], Sxy = S[1], Sxz = S[2], Syx = S[3], Syy = S[4], Syz = S[5], Szx = S[6], Szy = S[7],
+                 Szz = S[8];
+    double N[4][4] = {{Sxx + Syy + Szz, Syz - Szy, Szx - Sxz, Sxy - Syx},
+                      {Syz - Szy, Sxx - Syy - Szz, Sxy + Syx, Szx + Sxz},
+                      {Szx - Sxz, Sxy + Syx, -Sxx + Syy - Szz, Syz + Szy},
+                      {Sxy - Syx, Szx + Sxz, Syz + Szy, -Sxx - Syy + Szz}};
+    double V[4][4] = {{1, 0, 0, 0}, {0, 1, 0, 0}, {0, 0, 1, 0}, {0, 0, 0, 1}};
+    // Cyclic Jacobi sweeps on the symmetric 4x4 matrix.
+    for (int sweep = 0; sweep < 50; ++sweep) {
+        double off = 0.0, tot = 0.0;
+        for (int p = 0; p < 4; ++p)
+            for (int q = 0; q < 4; ++q) {
+                tot += N[p][q] * N[p][q];
+                if (p != q) off += N[p][q] * N[p][q];
+            }
+        if (off <= 1e-32 * tot) break;
+        for (int p = 0; p < 3; ++p)
+            for (int q = p + 1; q < 4; ++q) {
+                if (N[p][q] == 0.0) continue;
+                const double theta = (N[q][q] - N[p][p]) / (2.0 * N[p][q]);
+                const double t = (theta >= 0 ? 1.0 : -1.0) / (std::fabs(theta) + std::sqrt(theta * theta + 1.0));
+                const double c = 1.0 / std::sqrt(t * t + 1.0), s = t * c;
+                for (int k = 0; k < 4; ++k) {
+                    const double a = N[k][p], b = N[k][q];
+                    N[k][p] = c * a - s * b;
+                    N[k][q] = s * a + c * b;
+                }
+                for (int k = 0; k < 4; ++k) {
+                    const double a = N[p][k], b = N[q][k];
+                    N[p][k] = c * a - s * b;
+                    N[q][k] = s * a + c * b;
+                }
+                for (int k = 0; k < 4; ++k) {
+                    const double a = V[k][p], b = V[k][q];
+                    V[k][p] = c * a - s * b;
+                    V[k][q] = s * a + c * b;
+                }
+            }
+    }
+    int best = 0;
+    for (int k = 1; k < 4; ++k)
+        if (N[k][k] > N[best][best]) best = k;
+    double q0 = V[0][best], q1 = V[1][best], q2 = V[2][best], q3 = V[3][best];
+    const double nq = std::sqrt(q0 * q0 + q1 * q1 + q2 * q2 + q3 * q3);
+    q0 /= nq; q1 /= nq; q2 /= nq; q3 /= nq;
+    R[0] = q0 * q0 + q1 * q1 - q2 * q2 - q3 * q3;
+    R[1] = 2 * (q1 * q2 - q0 * q3);
+    R[2] = 2 * (q1 * q3 + q0 * q2);
+    R[3] = 2 * (q1 * q2 + q0 * q3);
+    R[4] = q0 * q0 - q1 * q1 + q2 * q2 - q3 * q3;
+    R[5] = 2 * (q2 * q3 - q0 * q1);
+    R[6] = 2 * (q1 * q3 - q0 * q2);
+    R[7] = 2 * (q2 * q3 + q0 * q1);
+    R[8] = q0 * q0 - q1 * q1 - q2 * q2 + q3 * q3;
+    return N[best][best];
+}
+
+void ana_free(lbmd_t h) {
+    for (void *p : h->ana_allocs) cudaFree(p);
+    h->ana_allocs.clear();
+    h->ana = AnaArgs{};
+    h->ana_cov = nullptr;
+    h->ana_frames = h->ana_max = 0;
+}
+
+lbmd_status ana_alloc(lbmd_t h, void **p, size_t bytes) {
+    cudaError_t e = cudaMalloc(p, bytes < 16 ? 16 : bytes);
+    if (e != cudaSuccess) return cuda_fail(h, e, "cudaMalloc (analysis)");
+    h->ana_allocs.push_back(*p);
+    return LBMD_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -508,6 +621,8 @@ lbmd_status lbmd_create(const lbmd_params *params, int n_atoms, const double *ma
     CREATE_CK(cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming));
     CREATE_CK(cudaEventCreate(&h->ev_t0));
     CREATE_CK(cudaEventCreate(&h->ev_t1));
+    CREATE_CK(cudaEventCreate(&h->ev_m0));
+    CREATE_CK(cudaEventCreate(&h->ev_m1));
 
     const Lat &L = h->L;
     const size_t pop_bytes = L.N * Q * store_bytes(h->p.store);
@@ -611,6 +726,7 @@ lbmd_status lbmd_create(const lbmd_params *params, int n_atoms, const double *ma
         C.X = A.X;
         C.U = A.U;
         C.J = A.J;
+        C.order = A.order;
     }
     h->fix_grid = na > 0 ? (C.touched_cap + 255) / 256 : 1;
     CREATE_CK(cudaStreamSynchronize(h->stream));
@@ -626,11 +742,14 @@ void lbmd_destroy(lbmd_t h) {
     destroy_graph(h);
     for (void *p : h->allocs) cudaFree(p);
     for (void *p : h->adj_allocs) cudaFree(p);
+    for (void *p : h->ana_allocs) cudaFree(p);
     if (h->stage) cudaFree(h->stage);
     if (h->ev_fork) cudaEventDestroy(h->ev_fork);
     if (h->ev_join) cudaEventDestroy(h->ev_join);
     if (h->ev_t0) cudaEventDestroy(h->ev_t0);
     if (h->ev_t1) cudaEventDestroy(h->ev_t1);
+    if (h->ev_m0) cudaEventDestroy(h->ev_m0);
+    if (h->ev_m1) cudaEventDestroy(h->ev_m1);
     if (h->s_main) cudaStreamDestroy(h->s_main);
     if (h->s_lat) cudaStreamDestroy(h->s_lat);
     delete h;
@@ -801,6 +920,16 @@ lbmd_status lbmd_set_physics(lbmd_t h, double gamma, double tau, double force_am
     return LBMD_OK;
 }
 
+lbmd_status lbmd_set_thermal(lbmd_t h, double kT, uint64_t seed) {
+    if (!h) return fail(nullptr, LBMD_ERR_ARG, "handle is NULL");
+    if (!(kT >= 0.0) || !std::isfinite(kT)) return fail(h, LBMD_ERR_ARG, "kT must be finite and >= 0");
+    h->kT = kT;
+    h->seed = seed;
+    fill_physics(h);
+    destroy_graph(h);
+    return LBMD_OK;
+}
+
 lbmd_status lbmd_set_timing_events(lbmd_t h, void *ev_start, void *ev_stop) {
     if (!h) return fail(nullptr, LBMD_ERR_ARG, "handle is NULL");
     if ((ev_start == nullptr) != (ev_stop == nullptr)) return fail(h, LBMD_ERR_ARG, "give both events or neither");
@@ -814,6 +943,20 @@ lbmd_status lbmd_set_timing_events(lbmd_t h, void *ev_start, void *ev_stop) {
     return LBMD_OK;
 }
 
+lbmd_status lbmd_set_md_timing_events(lbmd_t h, void *ev_start, void *ev_stop) {
+    if (!h) return fail(nullptr, LBMD_ERR_ARG, "handle is NULL");
+    if ((ev_start == nullptr) != (ev_stop == nullptr)) return fail(h, LBMD_ERR_ARG, "give both events or neither");
+    if (!h->state_set) return fail(h, LBMD_ERR_STATE, "lbmd_set_state has not been called");
+    if (h->na == 0) return fail(h, LBMD_ERR_ARG, "no atoms: the step has no substep kernels");
+    if (!h->exec) TRY(build_graph(h));
+    if (!h->node_m0 || !h->node_m1) return fail(h, LBMD_ERR_CUDA, "substep timing nodes missing from the step graph");
+    cudaEvent_t a = ev_start ? (cudaEvent_t)ev_start : h->ev_m0;
+    cudaEvent_t b = ev_stop ? (cudaEvent_t)ev_stop : h->ev_m1;
+    CK(h, cudaGraphExecEventRecordNodeSetEvent(h->exec, h->node_m0, a));
+    CK(h, cudaGraphExecEventRecordNodeSetEvent(h->exec, h->node_m1, b));
+    return LBMD_OK;
+}
+
 lbmd_status lbmd_backward(lbmd_t h, int n_steps, int ckpt_every, int observable, double *d_gamma, double *d_tau,
                           double *d_force_amp, double *obs) {
     if (!h) return fail(nullptr, LBMD_ERR_ARG, "handle is NULL");
@@ -821,6 +964,8 @@ lbmd_status lbmd_backward(lbmd_t h, int n_steps, int ckpt_every, int observable,
     if (n_steps < 1 || ckpt_every < 1) return fail(h, LBMD_ERR_ARG, "need n_steps >= 1 and ckpt_every >= 1");
     if (observable != LBMD_OBS_DRAG_X && observable != LBMD_OBS_RG2) return fail(h, LBMD_ERR_ARG, "unknown observable");
     if (h->na == 0) return fail(h, LBMD_ERR_ARG, "the observables need atoms (n_atoms > 0)");
+    if (h->kT > 0.0)
+        return fail(h, LBMD_ERR_ARG, "the adjoint differentiates the deterministic step: set kT = 0 (lbmd_set_thermal)");
     TRY(adj_prepare(h, n_steps, ckpt_every));
     cudaStream_t s = h->stream;
     const int K = ckpt_every, nseg = (n_steps + K - 1) / K;
@@ -907,6 +1052,135 @@ lbmd_status lbmd_backward(lbmd_t h, int n_steps, int ckpt_every, int observable,
     if (d_gamma) *d_gamma = res[0];
     if (d_tau) *d_tau = -omh * om * om;
     if (d_force_amp) *d_force_amp = res[2] + corr[1];
+    return LBMD_OK;
+}
+
+lbmd_status lbmd_analysis_begin(lbmd_t h, int n_sel, const int32_t *sel, const double *x_ref, int max_frames) {
+    if (!h) return fail(nullptr, LBMD_ERR_ARG, "handle is NULL");
+    if (!h->state_set) return fail(h, LBMD_ERR_STATE, "lbmd_set_state has not been called");
+    if (h->na == 0) return fail(h, LBMD_ERR_ARG, "the observables need atoms (n_atoms > 0)");
+    if (max_frames < 1) return fail(h, LBMD_ERR_ARG, "max_frames must be >= 1");
+    const int n = sel ? n_sel : h->na;
+    if (n < 1 || n > h->na) return fail(h, LBMD_ERR_ARG, "n_sel must be in 1..n_atoms");
+    std::vector<int> idx(n);
+    for (int i = 0; i < n; ++i) {
+        idx[i] = sel ? sel[i] : i;
+        if (idx[i] < 0 || idx[i] >= h->na) return fail(h, LBMD_ERR_ARG, "selection index out of range");
+    }
+    // Reference: the caller's, or the selected atoms' current positions.
+    std::vector<double> y(3 * (size_t)n);
+    if (x_ref) {
+        for (size_t k = 0; k < y.size(); ++k) y[k] = x_ref[k];
+    } else {
+        std::vector<double> X(3 * (size_t)h->na);
+        CK(h, cudaMemcpyAsync(X.data(), h->A.X, X.size() * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+        CK(h, cudaStreamSynchronize(h->stream));
+        for (int d = 0; d < 3; ++d)
+            for (int i = 0; i < n; ++i) y[(size_t)d * n + i] = X[(size_t)d * h->na + idx[i]];
+    }
+    for (double v : y)
+        if (!std::isfinite(v)) return fail(h, LBMD_ERR_ARG, "x_ref holds a non-finite value");
+    const size_t M = 3 * (size_t)n;
+    if ((double)max_frames * (double)M * 4.0 > 64.0e9)
+        return fail(h, LBMD_ERR_ARG, "max_frames x 3 n_sel x 4 bytes of frame storage exceeds 64 GB");
+    ana_free(h);
+    std::vector<double> yc(y);
+    double ey = 0.0;
+    for (int d = 0; d < 3; ++d) {
+        double c = 0.0;
+        for (int i = 0; i < n; ++i) c += y[(size_t)d * n + i];
+        c /= n;
+        h->ana_ybar[d] = c;
+        for (int i = 0; i < n; ++i) {
+            yc[(size_t)d * n + i] -= c;
+            ey += yc[(size_t)d * n + i] * yc[(size_t)d * n + i];
+        }
+    }
+    h->ana_ey = ey;
+    AnaArgs &A = h->ana;
+    A.na = h->na;
+    A.n = n;
+    A.X = h->A.X;
+    A.mass = h->A.mass;
+    void *p;
+    TRY(ana_alloc(h, &p, n * sizeof(int))); A.sel = (const int *)p;
+    CK(h, cudaMemcpyAsync(p, idx.data(), n * sizeof(int), cudaMemcpyHostToDevice, h->stream));
+    TRY(ana_alloc(h, &p, M * sizeof(double))); A.y = (const double *)p;
+    CK(h, cudaMemcpyAsync(p, y.data(), M * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+    TRY(ana_alloc(h, &p, M * sizeof(double))); A.yc = (const double *)p;
+    CK(h, cudaMemcpyAsync(p, yc.data(), M * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+    TRY(ana_alloc(h, &p, (size_t)ana_blocks(A) * kAnaSums * sizeof(double))); A.partials = (double *)p;
+    TRY(ana_alloc(h, &p, kAnaSums * sizeof(double))); A.sums = (double *)p;
+    TRY(ana_alloc(h, &p, (size_t)max_frames * M * sizeof(float))); A.frames = (float *)p;
+    TRY(ana_alloc(h, &p, M * sizeof(double))); A.dsum = (double *)p;
+    CK(h, cudaMemsetAsync(p, 0, M * sizeof(double), h->stream));
+    TRY(ana_alloc(h, &p, M * sizeof(float))); A.meanf = (float *)p;
+    CK(h, cudaStreamSynchronize(h->stream));  // the host vectors go out of scope
+    h->ana_max = max_frames;
+    h->ana_frames = 0;
+    return LBMD_OK;
+}
+
+lbmd_status lbmd_analysis_frame(lbmd_t h, double *rg2, double *rmsd) {
+    if (!h) return fail(nullptr, LBMD_ERR_ARG, "handle is NULL");
+    if (!h->ana.frames) return fail(h, LBMD_ERR_STATE, "lbmd_analysis_begin has not been called");
+    if (h->ana_frames >= h->ana_max) return fail(h, LBMD_ERR_ARG, "max_frames frames already taken");
+    AnaArgs &A = h->ana;
+    A.X = h->A.X;
+    CK(h, launch_ana_moments(A, h->stream));
+    double m[kAnaSums];
+    CK(h, cudaMemcpyAsync(m, A.sums, sizeof(m), cudaMemcpyDeviceToHost, h->stream));
+    CK(h, cudaStreamSynchronize(h->stream));
+    for (double v : m)
+        if (!std::isfinite(v)) return fail(h, LBMD_ERR_NONFINITE, "non-finite atom position");
+    const double n = A.n;
+    AnaFit F{};
+    double ex = m[8];
+    for (int d = 0; d < 3; ++d) {
+        F.xbar[d] = m[5 + d] / n;
+        F.ybar[d] = h->ana_ybar[d];
+        ex -= n * F.xbar[d] * F.xbar[d];
+    }
+    // sum x_a yc_b = sum (x - xbar)_a yc_b, since yc sums to zero.
+    const double lambda = horn_rotation(m + 9, F.R);
+    if (rmsd) *rmsd = std::sqrt(std::max(0.0, (ex + h->ana_ey - 2.0 * lambda) / n));
+    if (rg2) {
+        const double M = m[0];
+        const double c[3] = {m[1] / M, m[2] / M, m[3] / M};
+        *rg2 = std::max(0.0, m[4] / M - (c[0] * c[0] + c[1] * c[1] + c[2] * c[2]));
+    }
+    CK(h, launch_ana_store(A, h->ana_frames, F, h->stream));
+    ++h->ana_frames;
+    return LBMD_OK;
+}
+
+lbmd_status lbmd_analysis_result(lbmd_t h, double *mean_disp, double *rmsf, float *cov, int on_device) {
+    if (!h) return fail(nullptr, LBMD_ERR_ARG, "handle is NULL");
+    if (!h->ana.frames) return fail(h, LBMD_ERR_STATE, "lbmd_analysis_begin has not been called");
+    if (h->ana_frames < 1) return fail(h, LBMD_ERR_STATE, "no frame taken (lbmd_analysis_frame)");
+    AnaArgs &A = h->ana;
+    const size_t n = A.n, M = 3 * n;
+    double *dmean = mean_disp, *drmsf = rmsf;
+    float *dcov = cov;
+    void *p = nullptr;
+    if (!on_device) {
+        CK(h, stage(h, (M + n) * sizeof(double), &p));
+        dmean = mean_disp ? (double *)p : nullptr;
+        drmsf = rmsf ? (double *)p + M : nullptr;
+        if (cov && !h->ana_cov) {
+            void *c;
+            TRY(ana_alloc(h, &c, M * M * sizeof(float)));
+            h->ana_cov = (float *)c;
+        }
+        dcov = cov ? h->ana_cov : nullptr;
+    }
+    CK(h, launch_ana_result(A, h->ana_frames, dmean, drmsf, dcov, h->stream));
+    if (!on_device) {
+        if (mean_disp) CK(h, cudaMemcpyAsync(mean_disp, dmean, M * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+        if (rmsf) CK(h, cudaMemcpyAsync(rmsf, drmsf, n * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+        if (cov) CK(h, cudaMemcpyAsync(cov, dcov, M * M * sizeof(float), cudaMemcpyDeviceToHost, h->stream));
+        CK(h, cudaStreamSynchronize(h->stream));
+    }
     return LBMD_OK;
 }
 

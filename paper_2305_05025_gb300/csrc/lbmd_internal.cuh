@@ -39,7 +39,7 @@ __host__ __device__ __forceinline__ constexpr float wgt(int i) {
 }
 
 // Device error flags (bit mask), raised with atomicOr, read by the host.
-enum : int { FLAG_NONFINITE = 1, FLAG_CELL = 2, FLAG_WALL = 4, FLAG_TOUCHED = 8 };
+enum : int { FLAG_NONFINITE = 1, FLAG_CELL = 2, FLAG_WALL = 4, FLAG_TOUCHED = 8, FLAG_TIMEOUT = 16 };
 
 // Device-resident step state, updated by the last kernel of each step.
 struct DevState {
@@ -102,7 +102,97 @@ struct Lat {
     float famp;   // body-force amplitude
     int fdir, faxis;
     const float *kshape;  // Kolmogorov wave sin(2 pi c / n_axis), c < n_axis (device table)
+    int thermal;          // 1: add the thermal noise xi_i after every collision
+    float namp[15];       // noise amplitude of modes 4..18: sqrt(mu (1 - (1 - omega)^2) / b_k)
+    unsigned key0, key1;  // noise seed (low, high words)
 };
+
+// ---------------------------------------------------------------------------
+// Thermal noise of the fluctuating lattice Boltzmann equation: the xi_i of the
+// source term S_i = p_i + xi_i of Eq. (1) (Sec. 2.2). After the collision each
+// node gets xi_i = w_i sum_{k=4..18} e_k(c_i) a_k n_k: independent standard
+// normals n_k on the 15 modes e_k of a moment basis that are not conserved
+// (the basis polynomials below are orthogonal under the weights w_i; modes
+// 0..3, density and momentum, get none), with a_k = sqrt(mu (1 - (1 -
+// omega)^2) / b_k), b_k = sum_i w_i e_k(c_i)^2, mu = rho0 kT / c_s^2: each
+// mode then fluctuates with variance mu b_k at rest, as the
+// fluctuation-dissipation relation of a relaxation by 1 - omega requires.
+// The normals come from the counter-based Philox4x32-10 generator (counter:
+// node, block 0..3, step; key: the seed), 23-bit uniforms (m + 1/2) 2^-23,
+// and the Box-Muller transform.
+
+// Mode k of the basis at speed i (small integers; constant-folded).
+__host__ __device__ __forceinline__ constexpr int emode(int k, int i) {
+    const int x = cx(i), y = cy(i), z = cz(i), c2 = x * x + y * y + z * z;
+    return k == 0    ? 1
+           : k == 1  ? x
+           : k == 2  ? y
+           : k == 3  ? z
+           : k == 4  ? c2 - 1
+           : k == 5  ? 3 * x * x - c2
+           : k == 6  ? y * y - z * z
+           : k == 7  ? x * y
+           : k == 8  ? y * z
+           : k == 9  ? x * z
+           : k == 10 ? (3 * c2 - 5) * x
+           : k == 11 ? (3 * c2 - 5) * y
+           : k == 12 ? (3 * c2 - 5) * z
+           : k == 13 ? (y * y - z * z) * x
+           : k == 14 ? (z * z - x * x) * y
+           : k == 15 ? (x * x - y * y) * z
+           : k == 16 ? 3 * c2 * c2 - 6 * c2 + 1
+           : k == 17 ? (2 * c2 - 3) * (3 * x * x - c2)
+                     : (2 * c2 - 3) * (y * y - z * z);
+}
+
+// Philox4x32-10 block: ten rounds of the two 32x32 -> 64-bit products of the
+// published generator, the key advanced by its Weyl constants.
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, unsigned k0, unsigned k1) {
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const unsigned lo0 = 0xD2511F53u * c.x, hi0 = __umulhi(0xD2511F53u, c.x);
+        const unsigned lo1 = 0xCD9E8D57u * c.z, hi1 = __umulhi(0xCD9E8D57u, c.z);
+        c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+    return c;
+}
+
+// Two standard normals from two words (Box-Muller on 23-bit uniforms, exact in FP32).
+__device__ __forceinline__ float2 box_muller(unsigned a, unsigned b) {
+    const float u1 = ((float)(a >> 9) + 0.5f) * 1.1920928955078125e-7f;  // 2^-23
+    const float u2 = ((float)(b >> 9) + 0.5f) * 1.1920928955078125e-7f;
+    const float r = sqrtf(-2.f * logf(u1));
+    float sn, cs;
+    sincospif(2.f * u2, &sn, &cs);
+    return make_float2(r * cs, r * sn);
+}
+
+// xi_i of one node at one step, scaled by sc (the storage scale of the
+// stored deviations the caller adds it to).
+__device__ __forceinline__ void node_noise(const Lat &L, unsigned node, unsigned step, float sc, float xi[Q]) {
+    float s[16];
+#pragma unroll
+    for (int call = 0; call < 4; ++call) {
+        const uint4 w = philox4x32_10(make_uint4(node, (unsigned)call, step, 0u), L.key0, L.key1);
+        const float2 n0 = box_muller(w.x, w.y), n1 = box_muller(w.z, w.w);
+        s[4 * call] = n0.x;
+        s[4 * call + 1] = n0.y;
+        s[4 * call + 2] = n1.x;
+        s[4 * call + 3] = n1.y;
+    }
+#pragma unroll
+    for (int k = 0; k < 15; ++k) s[k] *= sc * L.namp[k];
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        float acc = 0.f;
+#pragma unroll
+        for (int k = 4; k < Q; ++k)
+            if (emode(k, i) != 0) acc = fmaf((float)emode(k, i), s[k - 4], acc);
+        xi[i] = wgt(i) * acc;
+    }
+}
 
 // Body force g at a node (the Kolmogorov wave from a per-row table, L1-resident).
 __device__ __forceinline__ void body_force(const Lat &L, int x, int y, int z, float g[3]) {
@@ -482,6 +572,7 @@ struct CouplingArgs {
     int *touched;   // unique touched nodes of this step
     int touched_cap;
     float4 *G;      // per node coupling force (x, y, z, unused)
+    const int *order;  // atoms in warp-sorted (Morton bucket) order, as AtomArgs::order
     DevState *ds;
     int keep;       // 1: the fix-up leaves G and the touched list for the adjoint
 };
@@ -499,6 +590,29 @@ struct AdjArgs {
     double *partials;         // 2*nblocks: block sums of d/d omega and d/d A
     float obs_w;              // 1/T
     int observable;
+};
+
+// Trajectory analysis (observables of the solute). Frame moments, FP64:
+// [0] sum m, [1..3] sum m x, [4] sum m |x|^2 over all atoms; over the
+// selection [5..7] sum x, [8] sum |x|^2, [9 + 3a + b] sum x_a yc_b (yc: the
+// reference minus its centroid).
+constexpr int kAnaSums = 18;
+struct AnaArgs {
+    int na, n;            // atoms, selected atoms
+    const double *X;      // 3*na FP64 positions
+    const float *mass;    // na
+    const int *sel;       // n atom indices
+    const double *y;      // 3n reference positions (SoA)
+    const double *yc;     // 3n reference minus its centroid
+    double *partials;     // ana_blocks * kAnaSums
+    double *sums;         // kAnaSums
+    float *frames;        // max_frames rows of 3n superposed displacements (component-major)
+    double *dsum;         // 3n running sum of the displacements
+    float *meanf;         // 3n mean displacement (FP32, set at the result)
+};
+struct AnaFit {
+    double R[9];          // rotation, row-major
+    double xbar[3], ybar[3];
 };
 
 // Message returned by lbmd_last_error(NULL) on the calling thread.
@@ -532,6 +646,11 @@ cudaError_t launch_rg2_grad(const AtomArgs &A, double *scratch, float w, float *
 cudaError_t launch_sum_double(const double *v, int n, double *out, cudaStream_t s);
 
 cudaError_t launch_interp(int store, const CouplingArgs &c, const AtomArgs &a, void *const buf[2], cudaStream_t s);
+
+int ana_blocks(const AnaArgs &A);
+cudaError_t launch_ana_moments(const AnaArgs &A, cudaStream_t s);
+cudaError_t launch_ana_store(const AnaArgs &A, int frame, const AnaFit &F, cudaStream_t s);
+cudaError_t launch_ana_result(const AnaArgs &A, int T, double *mean, double *rmsf, float *cov, cudaStream_t s);
 cudaError_t launch_spread(const CouplingArgs &c, cudaStream_t s);
 
 }  // namespace lbmd

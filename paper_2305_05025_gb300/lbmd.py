@@ -78,13 +78,19 @@ def lib():
         L.lbmd_cell_list.argtypes = [vp, vp, vp, vp, ip]
         L.lbmd_set_physics.argtypes = [vp, C.c_double, C.c_double, C.c_double]
         L.lbmd_set_timing_events.argtypes = [vp, vp, vp]
+        L.lbmd_set_md_timing_events.argtypes = [vp, vp, vp]
+        L.lbmd_set_thermal.argtypes = [vp, C.c_double, C.c_uint64]
+        L.lbmd_analysis_begin.argtypes = [vp, ip, vp, vp, ip]
+        L.lbmd_analysis_frame.argtypes = [vp, dp, dp]
+        L.lbmd_analysis_result.argtypes = [vp, vp, vp, vp, ip]
         L.lbmd_backward.argtypes = [vp, ip, ip, ip, dp, dp, dp, dp]
         L.lbmd_last_error.argtypes = [vp]
         L.lbmd_last_error.restype = C.c_char_p
         L.lbmd_destroy.argtypes = [vp]
         L.lbmd_destroy.restype = None
         for name in ("lbmd_create", "lbmd_set_state", "lbmd_step", "lbmd_get_fields", "lbmd_get_stats",
-                     "lbmd_check", "lbmd_cell_list", "lbmd_set_physics", "lbmd_set_timing_events",
+                     "lbmd_check", "lbmd_cell_list", "lbmd_set_physics", "lbmd_set_timing_events", "lbmd_set_md_timing_events",
+                     "lbmd_analysis_begin", "lbmd_analysis_frame", "lbmd_analysis_result", "lbmd_set_thermal",
                      "lbmd_backward", "lbmd_version"):
             getattr(L, name).restype = C.c_int
         _lib = L
@@ -253,6 +259,11 @@ def lbmd_set_physics(h, gamma, tau, force_amp):
     h.params.gamma, h.params.tau, h.params.force_amp = float(gamma), float(tau), float(force_amp)
 
 
+def lbmd_set_thermal(h, kT, seed=0):
+    """Thermal noise of the fluid: kT > 0 turns it on (see include/lbmd.h)."""
+    _check(h, lib().lbmd_set_thermal(h, float(kT), int(seed) & 0xFFFFFFFFFFFFFFFF))
+
+
 def lbmd_set_timing_events(h, ev_start=None, ev_stop=None):
     """ev_start/ev_stop: torch.cuda.Event(enable_timing=True) or raw cudaEvent_t
     handles; None restores the library's own events."""
@@ -263,12 +274,51 @@ def lbmd_set_timing_events(h, ev_start=None, ev_stop=None):
     _check(h, lib().lbmd_set_timing_events(h, raw(ev_start), raw(ev_stop)))
 
 
+def lbmd_set_md_timing_events(h, ev_start=None, ev_stop=None):
+    """Events around the substep kernels of the next step launches (see
+    lbmd_set_timing_events)."""
+    def raw(e):
+        if e is None:
+            return None
+        return C.c_void_p(e.cuda_event if hasattr(e, "cuda_event") else int(e))
+    _check(h, lib().lbmd_set_md_timing_events(h, raw(ev_start), raw(ev_stop)))
+
+
 def lbmd_backward(h, n_steps, ckpt_every, observable=OBS_DRAG_X):
     """Returns (observable, d/dgamma, d/dtau, d/dforce_amp)."""
     vals = [C.c_double() for _ in range(4)]
     _check(h, lib().lbmd_backward(h, int(n_steps), int(ckpt_every), int(observable),
                                   C.byref(vals[0]), C.byref(vals[1]), C.byref(vals[2]), C.byref(vals[3])))
     return vals[3].value, vals[0].value, vals[1].value, vals[2].value
+
+
+def lbmd_analysis_begin(h, sel=None, x_ref=None, max_frames=1):
+    """Starts a trajectory analysis of the atoms `sel` (None: all) against the
+    reference x_ref (3, n_sel) (None: their current positions)."""
+    keep = []
+    n = h.n_atoms if sel is None else len(sel)
+    ps, _ = (None, None) if sel is None else _ptr(np.asarray(sel, np.int32), np.int32, (n,), keep)
+    pr, _ = (None, None) if x_ref is None else _ptr(np.asarray(x_ref, np.float64), np.float64, (3, n), keep)
+    _check(h, lib().lbmd_analysis_begin(h, int(n), ps, pr, int(max_frames)))
+    h.ana_n = n
+
+
+def lbmd_analysis_frame(h):
+    """Returns (R_g^2 of all atoms, RMSD of the selection after superposition)."""
+    rg2, rmsd = C.c_double(), C.c_double()
+    _check(h, lib().lbmd_analysis_frame(h, C.byref(rg2), C.byref(rmsd)))
+    return rg2.value, rmsd.value
+
+
+def lbmd_analysis_result(h, cov=True):
+    """Returns (mean displacement (3, n), RMSF (n,), covariance (3n, 3n) FP32 or None)."""
+    n = h.ana_n
+    mean = np.zeros((3, n))
+    rmsf = np.zeros(n)
+    c = np.zeros((3 * n, 3 * n), np.float32) if cov else None
+    p = lambda a: None if a is None else a.ctypes.data_as(C.c_void_p)
+    _check(h, lib().lbmd_analysis_result(h, p(mean), p(rmsf), p(c), 0))
+    return mean, rmsf, c
 
 
 def lbmd_destroy(h):
