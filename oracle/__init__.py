@@ -35,13 +35,15 @@ class _Params(C.Structure):
                 ("forcing", C.c_int), ("force_amp", C.c_double),
                 ("force_dir", C.c_int), ("force_wave_axis", C.c_int),
                 ("walls_z", C.c_int), ("brute_force", C.c_int),
-                ("kT", C.c_double), ("seed", C.c_uint64), ("step0", C.c_int64)]
+                ("kT", C.c_double), ("seed", C.c_uint64), ("step0", C.c_int64),
+                ("coul_c", C.c_double), ("coul_rc", C.c_double)]
 
 
 class _Topology(C.Structure):
     _fields_ = [("n_atoms", C.c_int), ("mass", C.POINTER(C.c_double)),
                 ("n_bonds", C.c_int), ("bonds", C.POINTER(C.c_int32)),
-                ("bond_k", C.POINTER(C.c_double)), ("bond_r0", C.POINTER(C.c_double))]
+                ("bond_k", C.POINTER(C.c_double)), ("bond_r0", C.POINTER(C.c_double)),
+                ("charge", C.POINTER(C.c_double))]
 
 
 _lib = None
@@ -83,14 +85,16 @@ def params(cfg, brute_force=False):
                    forcing, float(cfg.get("force_amp", 0.0)),
                    int(cfg.get("force_dir", 0)), int(cfg.get("force_wave_axis", 1)),
                    int(cfg.get("walls_z", 0)), int(bool(brute_force)),
-                   float(cfg.get("kT", 0.0)), int(cfg.get("seed", 0)), int(cfg.get("step0", 0)))
+                   float(cfg.get("kT", 0.0)), int(cfg.get("seed", 0)), int(cfg.get("step0", 0)),
+                   float(cfg.get("coul_c", 0.0)), float(cfg.get("coul_rc", rcut)))
 
 
 class Topology:
     """Holds contiguous copies of the atom topology for the C call."""
 
-    def __init__(self, mass, bonds, bond_k, bond_r0):
+    def __init__(self, mass, bonds, bond_k, bond_r0, charge=None):
         self.mass = np.ascontiguousarray(mass, dtype=np.float64)
+        self.charge = None if charge is None else np.ascontiguousarray(charge, dtype=np.float64)
         self.bonds = np.ascontiguousarray(np.asarray(bonds, dtype=np.int32).reshape(-1, 2))
         self.bond_k = np.ascontiguousarray(bond_k, dtype=np.float64)
         self.bond_r0 = np.ascontiguousarray(bond_r0, dtype=np.float64)
@@ -103,7 +107,8 @@ class Topology:
             self.bond_k = np.zeros(1)
             self.bond_r0 = np.zeros(1)
         self.s = _Topology(len(self.mass), _d(self.mass), self.nb, _i(self.bonds),
-                           _d(self.bond_k), _d(self.bond_r0))
+                           _d(self.bond_k), _d(self.bond_r0),
+                           None if self.charge is None else _d(self.charge))
 
 
 def lattice():

@@ -48,6 +48,12 @@
  *      and key (seed low, seed high); uniforms ((w >> 9) + 1/2) 2^-23 (exact
  *      in FP32 as in FP64, so a single-precision implementation draws the
  *      same uniforms); normals by the Box-Muller transform.
+ *  R12 Electrostatics (Sec. 2.2: Coulomb interactions with a distance-dependent
+ *      dielectric and a cutoff, in the paper's implicit-solvent force field):
+ *      with charges q, the pair energy k q_a q_b / (eps(r) r) with
+ *      eps(r) = eps_r r is C q_a q_b / r^2, C = k / eps_r, shifted-force at
+ *      the cutoff r_cc (force and energy vanish there), for non-bonded pairs
+ *      within r_cc <= the Lennard-Jones cutoff; off when no charges are given.
  */
 #define _DEFAULT_SOURCE
 #include <math.h>
@@ -91,6 +97,8 @@ typedef struct {
     double kT;                        /* thermal energy of the fluctuating LB (0: no noise) */
     uint64_t seed;                    /* key of the noise's random numbers */
     int64_t step0;                    /* step index of the first step of a run */
+    double coul_c;                    /* C = k / eps_r of the screened Coulomb pairs (R12) */
+    double coul_rc;                   /* their cutoff (<= lj_rcut) */
 } orc_params;
 
 typedef struct {
@@ -100,6 +108,7 @@ typedef struct {
     const int32_t *bonds;  /* 2 * n_bonds atom indices */
     const double *bond_k;
     const double *bond_r0;
+    const double *charge;  /* n_atoms charges, or NULL: no electrostatics */
 } orc_topology;
 
 enum { ORC_OK = 0, ORC_ERR_ARG = -1, ORC_ERR_ALLOC = -2, ORC_ERR_WALL = -3 };
@@ -409,6 +418,16 @@ static void lj_shifted_force(const orc_params *p, double r, double *fmag, double
     *u = ur - uc + (r - p->lj_rcut) * fc;
 }
 
+/* Screened Coulomb pair (R12): energy C q_a q_b / r^2, radial force
+ * 2 C q_a q_b / r^3 (positive = repulsive), shifted so that force and energy
+ * vanish at coul_rc. qq = q_a q_b. */
+static void coulomb_shifted_force(const orc_params *p, double qq, double r, double *fmag, double *u) {
+    const double rc = p->coul_rc, A = p->coul_c * qq;
+    const double fr = 2.0 * A / (r * r * r), fc = 2.0 * A / (rc * rc * rc);
+    *fmag = fr - fc;
+    *u = A / (r * r) - A / (rc * rc) + (r - rc) * fc;
+}
+
 typedef struct {
     int n;
     int *start; /* n+1 */
@@ -570,6 +589,7 @@ typedef struct {
     double *F;
     double energy2; /* every pair is visited twice */
     int32_t *counts;
+    const double *charge; /* or NULL */
 } pair_ctx;
 
 static void visit_force(void *vctx, int a, int b) {
@@ -581,6 +601,12 @@ static void visit_force(void *vctx, int a, int b) {
     if (bonded(c->adj, a, b)) return;
     double r = sqrt(r2), fmag, u;
     lj_shifted_force(c->p, r, &fmag, &u);
+    if (c->charge && r2 < c->p->coul_rc * c->p->coul_rc) {
+        double fq, uq;
+        coulomb_shifted_force(c->p, c->charge[a] * c->charge[b], r, &fq, &uq);
+        fmag += fq;
+        u += uq;
+    }
     for (int k = 0; k < 3; ++k) c->F[k * c->na + a] += fmag * d[k] / r;
     c->energy2 += u;
 }
@@ -596,7 +622,7 @@ static int forces_with(const orc_params *p, const orc_topology *t, const adjacen
                        const double *x, double *F, double *energy) {
     int na = t->n_atoms;
     for (int k = 0; k < 3 * na; ++k) F[k] = 0.0;
-    pair_ctx ctx = {p, na, x, adj, F, 0.0, NULL};
+    pair_ctx ctx = {p, na, x, adj, F, 0.0, NULL, t->charge};
     int err = for_candidate_pairs(p, na, x, visit_force, &ctx);
     if (err) return err;
     double e = 0.5 * ctx.energy2;
@@ -626,7 +652,7 @@ int orc_forces(const orc_params *p, const orc_topology *t, const double *x, doub
 /* Number of other atoms within the LJ cutoff (strict r^2 < rc^2, FP64). */
 int orc_neighbour_counts(const orc_params *p, int n_atoms, const double *x, int32_t *counts) {
     for (int a = 0; a < n_atoms; ++a) counts[a] = 0;
-    pair_ctx ctx = {p, n_atoms, x, NULL, NULL, 0.0, counts};
+    pair_ctx ctx = {p, n_atoms, x, NULL, NULL, 0.0, counts, NULL};
     return for_candidate_pairs(p, n_atoms, x, visit_count, &ctx);
 }
 
@@ -699,6 +725,7 @@ static int check_params(const orc_params *p, const orc_topology *t) {
         return ORC_ERR_ARG;
     if (p->walls_z && p->nz < 2) return ORC_ERR_ARG;
     if (!(p->kT >= 0.0)) return ORC_ERR_ARG;
+    if (t->charge && !(p->coul_rc > 0.0 && p->coul_rc <= p->lj_rcut)) return ORC_ERR_ARG;
     return ORC_OK;
 }
 

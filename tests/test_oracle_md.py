@@ -336,3 +336,64 @@ def test_total_momentum_with_unequal_masses(orc):
     P1 = j1.sum(1) + (mass * v2).sum(1)
     assert np.allclose(P1, P0, rtol=0, atol=1e-12)
     assert np.abs((mass * (v2 - v)).sum(1)).max() > 1e-4  # the coupling moved momentum
+
+
+def _two(orc, r, q1, q2, bonded=False, **kw):
+    cfg = dict(nx=16, ny=16, nz=16, tau=1.0, lj_eps=0.0, coul_c=0.7, coul_rc=1.0)
+    cfg.update(kw)
+    b = np.array([[0, 1]]) if bonded else np.zeros((0, 2))
+    topo = orc.Topology(np.ones(2), b, [0.0] if bonded else [], [0.5] if bonded else [], charge=[q1, q2])
+    x = np.array([[5.0, 5.0 + r], [5.0, 5.0], [5.0, 5.0]])
+    F, e = orc.forces(cfg, topo, x)
+    return F, e
+
+
+def test_coulomb_pair_closed_form(orc):
+    """Energy C q1 q2 / r^2 (dielectric eps_r r), shifted-force at the cutoff:
+    radial force 2 C q1 q2 (1/r^3 - 1/rc^3); like charges repel."""
+    C, rc = 0.7, 1.0
+    for r, q1, q2 in ((0.5, 1.0, 1.0), (0.8, 1.0, -1.0), (0.3, -0.5, 2.0)):
+        F, e = _two(orc, r, q1, q2)
+        f = 2 * C * q1 * q2 * (1 / r ** 3 - 1 / rc ** 3)
+        assert np.isclose(F[0, 1], f, rtol=1e-13) and np.isclose(F[0, 0], -f, rtol=1e-13)
+        u = C * q1 * q2 * (1 / r ** 2 - 1 / rc ** 2) + (r - rc) * 2 * C * q1 * q2 / rc ** 3
+        assert np.isclose(e, u, rtol=1e-12)
+    F, _ = _two(orc, 0.5, 1.0, 1.0)
+    assert F[0, 1] > 0  # repulsion pushes atom 1 (at larger x) further out
+    F, e = _two(orc, 1.0 * (1 - 1e-9), 1.0, 1.0)
+    assert abs(F[0, 1]) < 1e-7 and abs(e) < 1e-9
+    assert _two(orc, 1.01, 1.0, 1.0)[1] == 0.0
+    # bonded pairs carry no Coulomb (a bond of zero stiffness leaves nothing)
+    F, e = _two(orc, 0.5, 1.0, 1.0, bonded=True)
+    assert np.abs(F).max() == 0.0 and e == 0.0
+
+
+def test_coulomb_forces_are_minus_energy_gradient(orc, c1):
+    """A charged chain (alternating +-1, LJ and bonds on): F = -grad U by
+    central differences, and the forces sum to zero (Newton's third law)."""
+    cfg, inp = c1
+    cfg = dict(cfg, coul_c=0.3, coul_rc=0.9)
+    q = np.where(np.arange(inp["x"].shape[1]) % 2 == 0, 1.0, -1.0)
+    topo = orc.Topology(inp["mass"], inp["bonds"], inp["bond_k"], inp["bond_r0"], charge=q)
+    rng = np.random.default_rng(12)
+    x = inp["x"] + 0.02 * rng.standard_normal(inp["x"].shape)
+    F, _ = orc.forces(cfg, topo, x)
+    F0, _ = orc.forces(cfg, orc.Topology(inp["mass"], inp["bonds"], inp["bond_k"], inp["bond_r0"]), x)
+    assert np.abs(F - F0).max() > 1e-2  # the charges act
+    assert np.abs(F.sum(1)).max() < 1e-9 * np.abs(F).max()
+    h = 1e-6
+    for a in rng.choice(x.shape[1], 12, replace=False):
+        for d in range(3):
+            xp, xm = x.copy(), x.copy()
+            xp[d, a] += h
+            xm[d, a] -= h
+            g = (orc.forces(cfg, topo, xp)[1] - orc.forces(cfg, topo, xm)[1]) / (2 * h)
+            assert abs(-g - F[d, a]) <= 1e-6 * max(1.0, abs(F[d, a]))
+
+
+def test_coulomb_cutoff_beyond_lennard_jones_is_rejected(orc):
+    cfg = dict(nx=8, ny=8, nz=8, tau=1.0, coul_c=1.0, coul_rc=1.5)
+    topo = orc.Topology(np.ones(2), np.zeros((0, 2)), [], [], charge=[1.0, -1.0])
+    f = orc.equilibrium(np.ones(512), np.zeros((3, 512)))
+    with pytest.raises(ValueError):
+        orc.run(cfg, topo, f, np.array([[2.0, 2.5], [2.0, 2.0], [2.0, 2.0]]), np.zeros((3, 2)), 1)
