@@ -36,7 +36,7 @@ class _Params(C.Structure):
                 ("force_dir", C.c_int), ("force_wave_axis", C.c_int),
                 ("walls_z", C.c_int), ("brute_force", C.c_int),
                 ("kT", C.c_double), ("seed", C.c_uint64), ("step0", C.c_int64),
-                ("coul_c", C.c_double), ("coul_rc", C.c_double)]
+                ("coul_c", C.c_double), ("coul_rc", C.c_double), ("reinterp", C.c_int)]
 
 
 class _Topology(C.Structure):
@@ -86,7 +86,8 @@ def params(cfg, brute_force=False):
                    int(cfg.get("force_dir", 0)), int(cfg.get("force_wave_axis", 1)),
                    int(cfg.get("walls_z", 0)), int(bool(brute_force)),
                    float(cfg.get("kT", 0.0)), int(cfg.get("seed", 0)), int(cfg.get("step0", 0)),
-                   float(cfg.get("coul_c", 0.0)), float(cfg.get("coul_rc", rcut)))
+                   float(cfg.get("coul_c", 0.0)), float(cfg.get("coul_rc", rcut)),
+                   int(cfg.get("reinterp", 0)))
 
 
 class Topology:

@@ -54,6 +54,13 @@
  *      eps(r) = eps_r r is C q_a q_b / r^2, C = k / eps_r, shifted-force at
  *      the cutoff r_cc (force and energy vanish there), for non-bonded pairs
  *      within r_cc <= the Lennard-Jones cutoff; off when no charges are given.
+ *  R13 Re-interpolation (an option, reinterp = 1; R7 stays the default): the
+ *      node velocities u_j stay those at the start of the step, but every
+ *      half-kick takes the fluid velocity interpolated at the atom's position
+ *      of that moment (x^s for the first half-kick of substep s, x^(s+1) for
+ *      the second), and its friction impulse is spread with the weights of
+ *      that same position, so the fluid still receives exactly the impulse
+ *      the atoms lose.
  */
 #define _DEFAULT_SOURCE
 #include <math.h>
@@ -99,6 +106,7 @@ typedef struct {
     int64_t step0;                    /* step index of the first step of a run */
     double coul_c;                    /* C = k / eps_r of the screened Coulomb pairs (R12) */
     double coul_rc;                   /* their cutoff (<= lj_rcut) */
+    int reinterp;                     /* 1: fluid velocity re-interpolated at every half-kick (R13) */
 } orc_params;
 
 typedef struct {
@@ -759,6 +767,37 @@ static int step_once(const orc_params *p, const orc_topology *t, const adjacency
             return err;
         }
         for (int k = 0; k < 3 * na; ++k) w->J[k] = 0.0;
+        if (p->reinterp) {
+            /* R13: U at the position of each half-kick, each impulse spread with
+             * the weights of that position. dJ holds minus the half-kick's impulse. */
+            double *dJ = (double *)malloc(sizeof(double) * 3 * (size_t)na);
+            if (!dJ) {
+                free(xs);
+                return ORC_ERR_ALLOC;
+            }
+            for (int s = 0; s < p->n_md && !err; ++s) {
+                for (int half = 0; half < 2 && !err; ++half) {
+                    if (half == 1) {
+                        for (int k = 0; k < 3 * na; ++k) x[k] += dt * v[k];
+                        err = forces_with(p, t, adj, x, w->F, NULL);
+                        if (!err) err = orc_interp(p, w->ub, na, x, w->U);
+                        if (err) break;
+                    }
+                    for (int a = 0; a < na; ++a)
+                        for (int d = 0; d < 3; ++d) {
+                            size_t q = (size_t)d * na + a;
+                            double drag = p->gamma * (w->U[q] - v[q]);
+                            w->J[q] += 0.5 * dt * drag;
+                            dJ[q] = -0.5 * dt * drag;
+                            v[q] += 0.5 * dt * (w->F[q] + drag) / t->mass[a];
+                        }
+                    if (!err) err = orc_spread(p, na, x, dJ, w->G);
+                }
+            }
+            free(dJ);
+            free(xs);
+            if (err) return err;
+        } else {
         for (int s = 0; s < p->n_md; ++s) {
             for (int a = 0; a < na; ++a)
                 for (int d = 0; d < 3; ++d) {
@@ -788,6 +827,7 @@ static int step_once(const orc_params *p, const orc_topology *t, const adjacency
         for (int k = 0; k < 3 * na; ++k) w->J[k] = -w->J[k];
         free(xs);
         if (err) return err;
+        }
     }
 
     /* Collision with the total force F = g + G (Eq. (1), R1, R4). */

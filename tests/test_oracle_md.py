@@ -397,3 +397,64 @@ def test_coulomb_cutoff_beyond_lennard_jones_is_rejected(orc):
     f = orc.equilibrium(np.ones(512), np.zeros((3, 512)))
     with pytest.raises(ValueError):
         orc.run(cfg, topo, f, np.array([[2.0, 2.5], [2.0, 2.0], [2.0, 2.0]]), np.zeros((3, 2)), 1)
+
+
+def _shear_step(orc, n_md, reinterp, S=1e-3, gamma=0.5, y0=4.3, vx0=0.0, vy0=0.05):
+    """One coupled step of one atom (m = 1, no forces) in a node velocity
+    field u_x = S (y - 4) (linear between the nodes it visits, so trilinear
+    interpolation is exact), u_y = u_z = 0. Returns (v_x, v_y, y) after it."""
+    n = 8
+    cfg = dict(nx=n, ny=n, nz=n, tau=0.8, gamma=gamma, n_md=n_md, reinterp=int(reinterp))
+    y = (np.arange(n ** 3) // n) % n
+    u = np.zeros((3, n ** 3))
+    u[0] = S * (y - 4.0)
+    f = orc.equilibrium(np.ones(n ** 3), u)
+    topo = orc.Topology(np.ones(1), np.zeros((0, 2)), [], [])
+    _, x2, v2, _ = orc.run(cfg, topo, f, np.array([[2.3], [y0], [3.6]]), np.array([[vx0], [vy0], [0.0]]), 1)
+    return v2[0, 0], v2[1, 0], x2[1, 0]
+
+
+@pytest.mark.parametrize("reinterp", [False, True])
+def test_coupling_converges_to_its_ode(orc, reinterp):
+    """Over one LB step the node velocities are frozen, so as n_md grows the
+    atom follows dv/dt = gamma (U - v) with U = S (y(t) - 4) e_x when the
+    velocity is re-interpolated at the current position, or U = S (y0 - 4) e_x
+    when it is held at the step's start. Closed forms (t = 1, m = 1):
+    v_y = v0 e^-g, y = y0 + v0 (1 - e^-g)/g, and
+    re-interpolated: v_x = S (y0 - 4 + v0/g)(1 - e^-g) - S v0 e^-g;
+    frozen:          v_x = S (y0 - 4)(1 - e^-g).
+    The half-kicks take the friction at the velocity they start from (the
+    second at v^(s+1/2)), which makes the velocity-dependent part first order:
+    the error halves per doubling of n_md, towards each coupling's own ODE."""
+    S, g, y0, v0 = 1e-3, 0.5, 4.3, 0.05
+    e = np.exp(-g)
+    vy = v0 * e
+    yy = y0 + v0 * (1 - e) / g
+    vx = S * (y0 - 4 + v0 / g) * (1 - e) - S * v0 * e if reinterp else S * (y0 - 4) * (1 - e)
+    errs = []
+    for n_md in (8, 16, 32, 64):
+        gx, gy, gyy = _shear_step(orc, n_md, reinterp)
+        errs.append(max(abs(gx - vx) / abs(vx), abs(gy - vy) / abs(vy), abs(gyy - yy) / abs(yy)))
+    ratios = [errs[i] / errs[i + 1] for i in range(3)]
+    assert all(1.9 < r < 2.1 for r in ratios), (errs, ratios)
+    assert errs[-1] < 2e-3
+    # The two couplings differ by the velocity gradient seen along the path.
+    fx, _, _ = _shear_step(orc, 64, not reinterp)
+    assert abs(fx - vx) > 10 * errs[-1] * abs(vx)
+
+
+def test_reinterpolated_coupling_conserves_momentum(orc, c1):
+    cfg, inp = c1
+    cfg = dict(cfg, nx=16, ny=16, nz=16, gamma=0.5, reinterp=1)
+    inp = synth.inputs(dict(cfg, chains=[dict(n=120, centre="box", radius=None)]), 2)
+    topo = _chain_topo(orc, inp)
+    rng = np.random.default_rng(15)
+    f = orc.equilibrium(np.ones(16 ** 3), 0.01 * rng.standard_normal((3, 16 ** 3)))
+    v = 0.1 * rng.standard_normal(inp["x"].shape)
+    r0, j0 = orc.moments(f)
+    f2, x2, v2, obs = orc.run(cfg, topo, f, inp["x"], v, 4)
+    r1, j1 = orc.moments(f2)
+    assert abs(r1.sum() - r0.sum()) < 1e-11
+    assert np.allclose(j1.sum(1) + v2.sum(1), j0.sum(1) + v.sum(1), rtol=0, atol=1e-12)
+    f3, x3, v3, _ = orc.run(dict(cfg, reinterp=0), topo, f, inp["x"], v, 4)
+    assert np.abs(v3 - v2).max() > 1e-6  # the option changes the dynamics
