@@ -77,26 +77,46 @@ def _peaks():
     return 6800.0, "fallback"
 
 
-def _kernel_hash():
+def _kernel_hash(files):
+    """Hash of the CUDA sources a kernel is built from: a recorded DRAM
+    traffic figure is valid only for the source it was measured on."""
     h = hashlib.sha256()
-    for f in ("lb.cu", "lbmd_internal.cuh"):
+    for f in files:
         with open(os.path.join(ROOT, "paper_2305_05025_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
 
 
-def _traffic(store, nodes):
-    """DRAM bytes per launch of the lattice kernel from the committed ncu
-    summary, if it was taken on the current kernel source; else None."""
-    p = os.path.join(ROOT, "profiles", "lb_step_traffic.json")
+LATTICE_SOURCES = ("lb.cu", "lbmd_internal.cuh")
+MD_SOURCES = ("md.cu", "lbmd_internal.cuh")
+
+
+def _recorded(name, key, sources):
+    """An entry of profiles/<name> (written from one ncu capture) if it was
+    taken on the current kernel source; else None."""
+    p = os.path.join(ROOT, "profiles", name)
     if not os.path.exists(p):
         return None
     with open(p) as fh:
         d = json.load(fh)
-    e = d.get(store)
-    if not e or e.get("kernel_hash") != _kernel_hash():
+    e = d.get(key)
+    if not e or e.get("kernel_hash") != _kernel_hash(sources):
         return None
-    return e["dram_bytes_per_node"] * nodes
+    return e
+
+
+def _traffic(store, nodes):
+    """DRAM bytes per launch of the lattice kernel (bytes per node from the
+    capture times the nodes of a launch), or None."""
+    e = _recorded("lb_step_traffic.json", store, LATTICE_SOURCES)
+    return None if e is None else e["dram_bytes_per_node"] * nodes
+
+
+def _md_traffic(na):
+    """DRAM bytes per launch of the substep kernel (per atom from the capture
+    times the atoms of a launch), or None."""
+    e = _recorded("md_substep_traffic.json", "k_md_substep", MD_SOURCES)
+    return None if e is None else e["dram_bytes_per_atom"] * na
 
 
 class Clocks:
@@ -240,6 +260,7 @@ def _config(cfg, inp, stores):
             "forcing": cfg["forcing"], "force_amp": cfg["force_amp"], "walls_z": cfg["walls_z"],
             "n_atoms": na, "n_md": cfg["n_md"], "gamma": cfg["gamma"], "skin": cfg["skin"],
             "store": stores[0], "compared_store": stores[1] if len(stores) > 1 else None,
+            "coupling": "re-interpolated at every substep" if cfg.get("reinterp") else "held over the step",
             "l2": f"inputs larger than L2: {lat / 1e6:.0f} MB of populations per step vs 126 MB L2"}
 
 
@@ -312,6 +333,8 @@ def timed_run(args, cfg, inp, store, local, barrier):
     c = dict(cfg, store=store)
     na = inp["x"].shape[1]
     h = lbmd.lbmd_create(c, inp["mass"], inp["bonds"], inp["bond_k"], inp["bond_r0"])
+    if args.reinterp:
+        lbmd.lbmd_set_reinterpolation(h, True)
     lbmd.lbmd_set_state(h, rho=inp["rho32"], u=inp["u32"], x=inp["x"], v=inp["v32"])
     stream = torch.cuda.current_stream()
     lbmd.lbmd_step(h, args.warmup)
@@ -431,11 +454,27 @@ def run_ours(args, cfg):
 
     launches = (n_md + 8) if na > 0 else 2  # 3 sort + interp + (n_md + 1) substeps + spread + dense + fix-up
     lat_roof = {s: _lattice_roofline(s, nodes, runs[s]["lb_ms"], hbm, peak_kind) for s in stores}
+    # The dominant kernel: the velocity-Verlet substep (n_md + 1 launches per
+    # step). Algorithmic bytes per atom and substep: ~100 (position hi + lo,
+    # velocity, force, interpolated velocity, impulse, drift, list length:
+    # read and written once), as the scope table's measurement row states.
+    md_us = prim["md_ms"] * 1e3 / (n_md + 1) if na > 0 else 0.0
+    md_roof = None
+    if na > 0:
+        md_achieved = 100.0 * na / (md_us * 1e-6) / 1e9
+        md_roof = {"bound": "hbm", "achieved": md_achieved, "peak": hbm, "unit": "GB/s", "frac": md_achieved / hbm,
+                   "traffic": _md_traffic(na),
+                   "kernel": f"k_md_substep (velocity-Verlet substep, {n_md + 1} launches per step, "
+                             f"{100 * prim['md_ms'] / (ms / args.steps):.0f}% of the step): 100 B per atom-substep "
+                             f"algorithmic x {na} atoms, {md_us:.1f} us per launch (CUDA events around the "
+                             f"substep chain on its stream); latency-bound (dependent neighbour-list loads), "
+                             f"peak {peak_kind} copy bandwidth"}
     out = {"metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
            "config": _config(cfg, inp, stores),
-           "roofline": lat_roof[stores[0]],
+           "roofline": md_roof if md_roof is not None else lat_roof[stores[0]],
+           "roofline_lattice": lat_roof[stores[0]],
            "e2e": ({"value": job_mlups(nodes, 1, world, e2e_s), "unit": "MLUPS", "h2d_bytes_per_step": io_bytes,
                     "d2h_bytes_per_step": io_bytes} if e2e_steps else None),
            "gpu_launches": args.steps * launches,
@@ -476,13 +515,22 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true", help="skip the timing of the adjoint workload")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end timing with host buffers")
+    ap.add_argument("--skin", type=float, default=None,
+                    help=f"Verlet-list skin (default {DEFAULT_OVERRIDES['skin']}): changes the speed, not the result")
+    ap.add_argument("--reinterp", action="store_true",
+                    help="re-interpolate the fluid velocity at every substep (the coupling variant; default: "
+                         "held over the step)")
     args = ap.parse_args()
     args.stores = [s.strip() for s in args.store.split(",") if s.strip()]
     for s in args.stores:
         if s not in ("f32", "f16", "bf16"):
             ap.error(f"unknown store {s}")
-    cfg = synth.workload(args.workload, **DEFAULT_OVERRIDES)
+    overrides = dict(DEFAULT_OVERRIDES)
+    if args.skin is not None:
+        overrides["skin"] = args.skin
+    cfg = synth.workload(args.workload, **overrides)
     cfg["store"] = args.stores[0]
+    cfg["reinterp"] = int(args.reinterp)
     if args.impl == "reference":
         world, rank, _ = _dist()
         if rank != 0:

@@ -170,6 +170,33 @@ lbmd_status lbmd_cell_list(lbmd_t h, int32_t *cell_of, int32_t *neighbours, int3
  * differentiates); the step graph is rebuilt on the next lbmd_step. */
 lbmd_status lbmd_set_physics(lbmd_t h, double gamma, double tau, double force_amp);
 
+/* Screened electrostatics of the solute (Sec. 2.2: the force field's Coulomb
+ * interactions with a distance-dependent dielectric and a cutoff). charge:
+ * n_atoms host doubles (NULL: no electrostatics, the default). Non-bonded
+ * pairs within coul_rc interact with the energy coul_c q_a q_b / r^2
+ * (k / (eps_r r) with eps_r r the dielectric: coul_c = k / eps_r), shifted so
+ * that force and energy vanish at coul_rc; coul_rc must be > 0 and no larger
+ * than the Lennard-Jones cutoff (the same pair lists serve both). Must be
+ * called before lbmd_set_state (LBMD_ERR_STATE after it), which computes the
+ * first forces with the charges. The adjoint includes the Coulomb pairs. */
+lbmd_status lbmd_set_charges(lbmd_t h, const double *charge, double coul_c, double coul_rc);
+
+/* Coupling variant (Sec. 2.2: the friction uses the fluid velocity "at the
+ * particle position"). on = 0 (the default): the velocity interpolated at the
+ * start of the step is held over its n_md substeps and the total friction
+ * impulse is spread with the step-start weights. on = 1: the node velocities
+ * stay those of the step's start, but every half-kick interpolates at the
+ * atom's position of that moment and each substep's impulse is spread with
+ * the weights of that position (the fluid still receives exactly what the
+ * atoms lose). The interpolation stores the node velocities of each atom's
+ * stencil and one node of margin; a substep that finds its atom beyond them
+ * computes the missing ones from the step's populations, so any displacement
+ * within a step is handled exactly. Costs one node-velocity array (16 bytes
+ * per node) and a touched-node list of 64 entries per atom (LBMD_ERR_STATE if
+ * the atoms claim more nodes in one step). The step graph is rebuilt on the
+ * next lbmd_step; lbmd_backward refuses on = 1. */
+lbmd_status lbmd_set_reinterpolation(lbmd_t h, int on);
+
 /* Thermal fluctuations of the fluid (Sec. 2.2: the noise xi_i of the
  * fluctuating lattice Boltzmann source term S_i = p_i + xi_i of Eq. 1, the
  * fluid acting as the heat bath). kT > 0 adds after every collision, at every
@@ -209,6 +236,15 @@ lbmd_status lbmd_set_md_timing_events(lbmd_t h, void *ev_start, void *ev_stop);
  * advanced by n_steps, as after lbmd_step(n_steps). */
 lbmd_status lbmd_backward(lbmd_t h, int n_steps, int ckpt_every, int observable, double *d_gamma,
                           double *d_tau, double *d_force_amp, double *obs);
+
+/* Like lbmd_backward, returning instead of the parameter gradients the
+ * gradient of the observable with respect to the initial state, in the
+ * ABI's terms: grad_f (19*N FP32, the post-streaming populations f_i of
+ * lbmd_set_state), grad_x and grad_v (3*n_atoms FP32 SoA, positions and
+ * velocities). Any output may be NULL; on_device as elsewhere. The same
+ * restrictions and state advance as lbmd_backward. */
+lbmd_status lbmd_backward_state(lbmd_t h, int n_steps, int ckpt_every, int observable, double *obs, float *grad_f,
+                                float *grad_x, float *grad_v, int on_device);
 
 /* Trajectory analysis of the solute (the analyses of Sec. 3 of the paper:
  * root-mean-square deviation from the starting structure, radius of

@@ -48,13 +48,13 @@
  *      and key (seed low, seed high); uniforms ((w >> 9) + 1/2) 2^-23 (exact
  *      in FP32 as in FP64, so a single-precision implementation draws the
  *      same uniforms); normals by the Box-Muller transform.
- *  R12 Electrostatics (Sec. 2.2: Coulomb interactions with a distance-dependent
+ *  R16 Electrostatics (Sec. 2.2: Coulomb interactions with a distance-dependent
  *      dielectric and a cutoff, in the paper's implicit-solvent force field):
  *      with charges q, the pair energy k q_a q_b / (eps(r) r) with
  *      eps(r) = eps_r r is C q_a q_b / r^2, C = k / eps_r, shifted-force at
  *      the cutoff r_cc (force and energy vanish there), for non-bonded pairs
  *      within r_cc <= the Lennard-Jones cutoff; off when no charges are given.
- *  R13 Re-interpolation (an option, reinterp = 1; R7 stays the default): the
+ *  R17 Re-interpolation (an option, reinterp = 1; R7 stays the default): the
  *      node velocities u_j stay those at the start of the step, but every
  *      half-kick takes the fluid velocity interpolated at the atom's position
  *      of that moment (x^s for the first half-kick of substep s, x^(s+1) for
@@ -104,9 +104,9 @@ typedef struct {
     double kT;                        /* thermal energy of the fluctuating LB (0: no noise) */
     uint64_t seed;                    /* key of the noise's random numbers */
     int64_t step0;                    /* step index of the first step of a run */
-    double coul_c;                    /* C = k / eps_r of the screened Coulomb pairs (R12) */
+    double coul_c;                    /* C = k / eps_r of the screened Coulomb pairs (R16) */
     double coul_rc;                   /* their cutoff (<= lj_rcut) */
-    int reinterp;                     /* 1: fluid velocity re-interpolated at every half-kick (R13) */
+    int reinterp;                     /* 1: fluid velocity re-interpolated at every half-kick (R17) */
 } orc_params;
 
 typedef struct {
@@ -426,7 +426,7 @@ static void lj_shifted_force(const orc_params *p, double r, double *fmag, double
     *u = ur - uc + (r - p->lj_rcut) * fc;
 }
 
-/* Screened Coulomb pair (R12): energy C q_a q_b / r^2, radial force
+/* Screened Coulomb pair (R16): energy C q_a q_b / r^2, radial force
  * 2 C q_a q_b / r^3 (positive = repulsive), shifted so that force and energy
  * vanish at coul_rc. qq = q_a q_b. */
 static void coulomb_shifted_force(const orc_params *p, double qq, double r, double *fmag, double *u) {
@@ -768,7 +768,7 @@ static int step_once(const orc_params *p, const orc_topology *t, const adjacency
         }
         for (int k = 0; k < 3 * na; ++k) w->J[k] = 0.0;
         if (p->reinterp) {
-            /* R13: U at the position of each half-kick, each impulse spread with
+            /* R17: U at the position of each half-kick, each impulse spread with
              * the weights of that position. dJ holds minus the half-kick's impulse. */
             double *dJ = (double *)malloc(sizeof(double) * 3 * (size_t)na);
             if (!dJ) {

@@ -310,8 +310,15 @@ __global__ void __launch_bounds__(128) k_adj_hvp(AdjArgs D, AtomArgs A, int k) {
             const float phi = A.lj_24eps * s6 * ir8 * (2.f * s6 * ir6 - 1.f) - A.lj_fc / r;
             // phi'/r = 24 eps s6 (-28 s6 r^-16 + 8 r^-10) + fc r^-3
             const float dphi_r = A.lj_24eps * s6 * ir8 * ir2 * (-28.f * s6 * ir6 + 8.f) + A.lj_fc * ir2 / r;
+            float ph = phi, dph = dphi_r;
+            if (A.coul && r2 < A.coul_rc2) {
+                // phi_q = 2 C q_a q_b (r^-4 - rcc^-3 r^-1), phi_q'/r = 2 C q_a q_b (-4 r^-6 + rcc^-3 r^-3)
+                const float c2 = A.coul_2c * pa.w * P[q].w;
+                ph += c2 * (ir2 * ir2 - A.coul_irc3 / r);
+                dph += c2 * (-4.f * ir6 + A.coul_irc3 * ir2 / r);
+            }
             const float dp[3] = {pA[0] - D.p[q], pA[1] - D.p[na + q], pA[2] - D.p[2 * na + q]};
-            hvp_add(phi, dphi_r, d, dp, out);
+            hvp_add(ph, dph, d, dp, out);
         }
     }
     for (int s = b0 + lane; s < b1; s += 32) {

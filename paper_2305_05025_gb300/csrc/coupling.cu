@@ -91,6 +91,14 @@ __global__ void __launch_bounds__(128) k_interp(CouplingArgs C, AtomArgs A, cons
     for (int d = 0; d < 3; ++d) {
         lo[d] = min(min(s_box[0][d], s_box[1][d]), min(s_box[2][d], s_box[3][d]));
         hi[d] = max(max(s_box[0][3 + d], s_box[1][3 + d]), max(s_box[2][3 + d], s_box[3][3 + d]));
+        if (C.reinterp) {  // one node of margin: where the atoms' stencils move in a typical step
+            lo[d] -= 1;
+            hi[d] += 1;
+            if (d == 2 && L.walls) {
+                lo[d] = max(lo[d], 0);
+                hi[d] = min(hi[d], L.nz - 1);
+            }
+        }
         ext[d] = hi[d] - lo[d] + 1;
     }
     const int tile = ext[0] * ext[1] * ext[2];  // > 0: every block holds at least one valid atom
@@ -100,15 +108,17 @@ __global__ void __launch_bounds__(128) k_interp(CouplingArgs C, AtomArgs A, cons
         for (int k = threadIdx.x; k < tile; k += blockDim.x) {
             const int ox = k % ext[0], oy = (k / ext[0]) % ext[1], oz = k / (ext[0] * ext[1]);
             int xx = lo[0] + ox, yy = lo[1] + oy, zz = lo[2] + oz;
-            xx -= xx >= L.nx ? L.nx : 0;
-            yy -= yy >= L.ny ? L.ny : 0;
-            zz -= zz >= L.nz ? L.nz : 0;
+            xx += xx < 0 ? L.nx : (xx >= L.nx ? -L.nx : 0);
+            yy += yy < 0 ? L.ny : (yy >= L.ny ? -L.ny : 0);
+            zz += zz < 0 ? L.nz : (zz >= L.nz ? -L.nz : 0);
             float f[Q], g[3], u[3];
             pull<S>(src, L, xx, yy, zz, f);
             body_force(L, xx, yy, zz, g);
             node_velocity(L, f, g, u);
             s_u[k] = make_float4(u[0], u[1], u[2], 0.f);
-            s_used[k] = 0;
+            s_used[k] = C.reinterp ? 1 : 0;  // re-interpolation claims the whole region
+            if (C.reinterp)
+                C.unode[((size_t)zz * L.ny + yy) * L.nx + xx] = make_float4(u[0], u[1], u[2], __int_as_float(stamp));
         }
         __syncthreads();
         if (valid) {
@@ -129,10 +139,38 @@ __global__ void __launch_bounds__(128) k_interp(CouplingArgs C, AtomArgs A, cons
             if (!s_used[k]) continue;
             const int ox = k % ext[0], oy = (k / ext[0]) % ext[1], oz = k / (ext[0] * ext[1]);
             int xx = lo[0] + ox, yy = lo[1] + oy, zz = lo[2] + oz;
-            xx -= xx >= L.nx ? L.nx : 0;
-            yy -= yy >= L.ny ? L.ny : 0;
-            zz -= zz >= L.nz ? L.nz : 0;
+            xx += xx < 0 ? L.nx : (xx >= L.nx ? -L.nx : 0);
+            yy += yy < 0 ? L.ny : (yy >= L.ny ? -L.ny : 0);
+            zz += zz < 0 ? L.nz : (zz >= L.nz ? -L.nz : 0);
             const int node = (int)(((size_t)zz * L.ny + yy) * L.nx + xx);
+            if (C.tag[node] != stamp && atomicExch(&C.tag[node], stamp) != stamp) {
+                const int j = atomicAdd(&C.ds->n_touched, 1);
+                if (j < C.touched_cap)
+                    C.touched[j] = node;
+                else
+                    atomicOr(&C.ds->flags, FLAG_TOUCHED);
+            }
+        }
+    } else if (valid && C.reinterp) {
+        // The atom's own region: its stencil and one node of margin.
+#pragma unroll 1
+        for (int k = 0; k < 64; ++k) {
+            const int o[3] = {(k & 3) - 1, ((k >> 2) & 3) - 1, (k >> 4) - 1};
+            if (L.walls && (b[2] + o[2] < 0 || b[2] + o[2] > L.nz - 1)) continue;
+            const int xx = wrapl((long long)b[0] + o[0], L.nx), yy = wrapl((long long)b[1] + o[1], L.ny),
+                      zz = wrapl((long long)b[2] + o[2], L.nz);
+            float f[Q], g[3], u[3];
+            pull<S>(src, L, xx, yy, zz, f);
+            body_force(L, xx, yy, zz, g);
+            node_velocity(L, f, g, u);
+            const int node = (int)(((size_t)zz * L.ny + yy) * L.nx + xx);
+            C.unode[node] = make_float4(u[0], u[1], u[2], __int_as_float(stamp));
+            if (o[0] >= 0 && o[0] <= 1 && o[1] >= 0 && o[1] <= 1 && o[2] >= 0 && o[2] <= 1) {
+                const float W = (o[0] ? t[0] : 1.f - t[0]) * (o[1] ? t[1] : 1.f - t[1]) * (o[2] ? t[2] : 1.f - t[2]);
+                U[0] += W * u[0];
+                U[1] += W * u[1];
+                U[2] += W * u[2];
+            }
             if (C.tag[node] != stamp && atomicExch(&C.tag[node], stamp) != stamp) {
                 const int j = atomicAdd(&C.ds->n_touched, 1);
                 if (j < C.touched_cap)
@@ -222,7 +260,7 @@ cudaError_t launch_interp(int store, const CouplingArgs &c, const AtomArgs &a, v
 }
 
 cudaError_t launch_spread(const CouplingArgs &c, cudaStream_t s) {
-    if (c.na == 0) return cudaSuccess;
+    if (c.na == 0 || c.reinterp) return cudaSuccess;  // re-interpolation: the substeps spread
     k_spread<<<(c.na + 127) / 128, 128, 0, s>>>(c);
     return cudaGetLastError();
 }

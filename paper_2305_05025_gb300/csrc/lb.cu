@@ -9,8 +9,6 @@
 // other. One thread per node, threads along x within a warp, so each of the 19
 // loads and stores of a warp is one contiguous run (shifted by one element for
 // speeds with c_x != 0).
-#include <algorithm>
-
 #include "lbmd_internal.cuh"
 
 namespace lbmd {
@@ -203,167 +201,6 @@ __global__ void __launch_bounds__(128, 7) k_lb_step_pair16(Lat L, typename Store
     for (int i = 0; i < Q; ++i, dp += plane) __stcs(reinterpret_cast<unsigned *>(dp), H::pack(fab[i].x, fab[i].y));
 }
 
-// ---------------------------------------------------------------------------
-// 16-bit storage, whole rows through shared memory. A persistent block walks
-// lattice rows (y, z); for each row one elected thread issues 19 bulk copies
-// (cp.async.bulk, completion counted on an mbarrier), one per population:
-// the whole source row the pull needs, (y - c_y, z - c_z), or the node's own
-// row of the opposite population where the pull would cross a z wall. Rows
-// are double-buffered, so the next row's 19 copies are in flight while this
-// one is collided. The x shift of the pull is then a shared-memory read
-// (periodic in x within the row) and a byte permute; each thread collides
-// node pairs (x0, x0 + 1) in packed FP32x2 as in k_lb_step_pair16 and
-// stores them with 32-bit streaming stores. Every wait on an mbarrier is
-// bounded (about a second): on expiry the block raises FLAG_TIMEOUT, waits
-// (bounded again) for its copies still in flight, and returns.
-
-__device__ __forceinline__ unsigned smem_addr(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ void mbar_init(unsigned long long *bar, unsigned count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ void mbar_expect_tx(unsigned long long *bar, unsigned bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
-                 : "memory");
-}
-
-__device__ __forceinline__ void bulk_copy_g2s(void *dst, const void *src, unsigned bytes, unsigned long long *bar) {
-    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                     smem_addr(dst)),
-                 "l"(src), "r"(bytes), "r"(smem_addr(bar))
-                 : "memory");
-}
-
-__device__ __forceinline__ bool mbar_test(unsigned long long *bar, unsigned parity) {
-    unsigned done;
-    asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
-        : "=r"(done)
-        : "r"(smem_addr(bar)), "r"(parity)
-        : "memory");
-    return done != 0;
-}
-
-// Waits for phase `parity` of the barrier for at most ~2^31 clock cycles
-// (about a second at 2 GHz); false on expiry.
-__device__ __forceinline__ bool mbar_wait_bounded(unsigned long long *bar, unsigned parity) {
-    const long long t0 = clock64();
-    while (!mbar_test(bar, parity))
-        if (clock64() - t0 > (1ll << 31)) return false;
-    return true;
-}
-
-constexpr int kRowThreads = 128;
-
-template <int S, int FD, bool TH>
-__global__ void __launch_bounds__(kRowThreads, 5) k_lb_step_rows16(Lat L, typename Store<S>::T *b0,
-                                                                 typename Store<S>::T *b1, DevState *ds) {
-    using T = typename Store<S>::T;
-    using H = Half16<S>;
-    extern __shared__ __align__(128) unsigned char s_rows[];  // [2][Q][nx] 16-bit values
-    __shared__ unsigned long long s_bar[2];
-    __shared__ int s_fail;
-    const int nx = L.nx, ny = L.ny, nz = L.nz, nxy = nx * ny;
-    const int nrows = ny * nz, half = nx / 2;
-    const unsigned row_bytes = (unsigned)nx * 2u;
-    const int step = ds->step;
-    const T *src = (step & 1) ? b1 : b0;
-    T *dst = (step & 1) ? b0 : b1;
-    const size_t plane = L.N;
-    auto stage = [&](int st, int i) { return reinterpret_cast<const unsigned *>(s_rows + ((size_t)st * Q + i) * row_bytes); };
-    // Copies of row r (y = r % ny, z = r / ny) into stage st, by one thread.
-    auto issue = [&](int r, int st) {
-        const int y = r % ny, z = r / ny;
-        mbar_expect_tx(&s_bar[st], Q * row_bytes);
-#pragma unroll 1
-        for (int i = 0; i < Q; ++i) {
-            const bool wall = L.walls && ((cz(i) == 1 && z == 0) || (cz(i) == -1 && z == nz - 1));
-            int q = i, ys = y, zs = z;
-            if (wall) {
-                q = opp(i);
-            } else {
-                ys = y - cy(i);
-                ys += ys < 0 ? ny : (ys >= ny ? -ny : 0);
-                zs = z - cz(i);
-                zs += zs < 0 ? nz : (zs >= nz ? -nz : 0);
-            }
-            const T *g = src + (size_t)q * plane + ((size_t)zs * ny + ys) * nx;
-            bulk_copy_g2s(s_rows + ((size_t)st * Q + i) * row_bytes, g, row_bytes, &s_bar[st]);
-        }
-    };
-    if (threadIdx.x == 0) {
-        mbar_init(&s_bar[0], 1);
-        mbar_init(&s_bar[1], 1);
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-        s_fail = 0;
-        if ((int)blockIdx.x < nrows) issue(blockIdx.x, 0);
-        if ((int)(blockIdx.x + gridDim.x) < nrows) issue(blockIdx.x + gridDim.x, 1);
-    }
-    __syncthreads();
-    int k = 0;
-    for (int r = blockIdx.x; r < nrows; r += gridDim.x, ++k) {
-        const int st = k & 1;
-        const unsigned parity = (unsigned)(k >> 1) & 1u;
-        if (!mbar_wait_bounded(&s_bar[st], parity)) s_fail = 1;
-        __syncthreads();
-        if (s_fail) break;
-        const int y = r % ny, z = r / ny;
-        const float ga = body_amp(L, 0, y, z);
-        for (int p = threadIdx.x; p < half; p += kRowThreads) {
-            float2 fab[Q];
-#pragma unroll
-            for (int i = 0; i < Q; ++i) {
-                const bool wall = L.walls && ((cz(i) == 1 && z == 0) || (cz(i) == -1 && z == nz - 1));
-                const unsigned *row = stage(st, i);
-                unsigned w;
-                if (cx(i) == 0 || wall) {
-                    w = row[p];
-                } else if (cx(i) == 1) {  // nodes x0, x0 + 1 pull x0 - 1, x0
-                    w = __byte_perm(row[p == 0 ? half - 1 : p - 1], row[p], 0x5432);
-                } else {  // nodes x0, x0 + 1 pull x0 + 1, x0 + 2
-                    w = __byte_perm(row[p], row[p + 1 == half ? 0 : p + 1], 0x5432);
-                }
-                fab[i] = H::unpack(w);
-            }
-            const float2 rr = collide_g2<FD, Store<S>::kScaled>(L, fab, ga);
-            if (!isfinite(rr.x) || !isfinite(rr.y)) atomicOr(&ds->flags, FLAG_NONFINITE);
-            const int node = z * nxy + y * nx + 2 * p;
-            if (TH) {
-                const float sc = Store<S>::kScaled ? kF16Scale : 1.f;
-                float xi[Q];
-                node_noise(L, (unsigned)node, (unsigned)step, sc, xi);
-#pragma unroll
-                for (int i = 0; i < Q; ++i) fab[i].x += xi[i];
-                node_noise(L, (unsigned)node + 1u, (unsigned)step, sc, xi);
-#pragma unroll
-                for (int i = 0; i < Q; ++i) fab[i].y += xi[i];
-            }
-            T *dp = dst + node;
-#pragma unroll
-            for (int i = 0; i < Q; ++i, dp += plane)
-                __stcs(reinterpret_cast<unsigned *>(dp), H::pack(fab[i].x, fab[i].y));
-        }
-        __syncthreads();  // stage st is read: refill it with the row after next
-        if (threadIdx.x == 0 && r + 2 * (int)gridDim.x < nrows) {
-            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // reads above before the copies' writes
-            issue(r + 2 * gridDim.x, st);
-        }
-    }
-    if (s_fail) {
-        // Let the copies still in flight land before the block's shared
-        // memory goes away (bounded again), and report.
-        if (threadIdx.x == 0) {
-            atomicOr(&ds->flags, FLAG_TIMEOUT);
-            for (int j = k; j < k + 2; ++j) {
-                const int r = blockIdx.x + j * gridDim.x;
-                if (r < nrows) mbar_wait_bounded(&s_bar[j & 1], (unsigned)(j >> 1) & 1u);
-            }
-        }
-        __syncthreads();
-    }
-}
-
 // Nodes touched by atoms: redo the collision with F = g + G from the same
 // pre-collision buffer, overwrite the dense kernel's result, clear G. The
 // last block to finish advances the step counter and empties the list.
@@ -410,6 +247,20 @@ __global__ void __launch_bounds__(256) k_lb_fix(Lat L, typename Store<S>::T *b0,
             __threadfence();
         }
     }
+}
+
+// dst_i(x) = src_i(x - c_i) (or src_opp(i)(x) behind a z wall) on FP32 arrays:
+// the pull of the streaming step, applied to adjoint fields.
+__global__ void k_pull_f32(Lat L, const float *src, float *dst) {
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    const int z = blockIdx.z;
+    if (x >= L.nx || y >= L.ny) return;
+    float f[Q];
+    pull<LBMD_F32>(src, L, x, y, z, f);
+    const size_t node = ((size_t)z * L.ny + y) * L.nx + x;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) dst[(size_t)i * L.N + node] = f[i];
 }
 
 template <int S>
@@ -608,44 +459,7 @@ dim3 node_grid(const Lat &L, dim3 b) { return dim3((L.nx + b.x - 1) / b.x, (L.ny
         LBMD_FD_DISPATCH1(L, BODY)                                         \
     }
 
-// Shared memory of the row kernel: two stages of 19 rows of nx 16-bit values.
-size_t rows16_smem(const Lat &L) { return (size_t)2 * Q * L.nx * 2; }
-
-// Row kernel for 16-bit storage: rows of whole 16-byte multiples (nx % 8 = 0)
-// that fit two stages in shared memory, body force uniform along x.
-bool use_rows16(int store, const Lat &L) {
-    return store != LBMD_F32 && L.nx % 8 == 0 && rows16_smem(L) <= 200 * 1024 &&
-           !(L.forcing == LBMD_FORCE_KOLMOGOROV && L.faxis == 0);
-}
-
-template <int SV, int FDV, bool THV>
-cudaError_t launch_rows16(const Lat &L, void *const buf[2], DevState *ds, cudaStream_t s) {
-    using T = typename Store<SV>::T;
-    const size_t smem = rows16_smem(L);
-    auto kern = k_lb_step_rows16<SV, FDV, THV>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    int per_sm = 0, dev = 0, sms = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kRowThreads, smem);
-    if (e != cudaSuccess) return e;
-    e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) return e;
-    e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (e != cudaSuccess) return e;
-    const long long rows = (long long)L.ny * L.nz;
-    const int grid = (int)std::min<long long>(rows, (long long)std::max(per_sm, 1) * sms);
-    kern<<<grid, kRowThreads, smem, s>>>(L, (T *)buf[0], (T *)buf[1], ds);
-    return cudaGetLastError();
-}
-
 cudaError_t launch_lb_step(int store, const Lat &L, void *const buf[2], DevState *ds, cudaStream_t s) {
-    if (use_rows16(store, L)) {
-        if (store == LBMD_F16_SHIFTED) {
-            LBMD_FD_DISPATCH(L, return (launch_rows16<LBMD_F16_SHIFTED, FDV, THV>(L, buf, ds, s)));
-        } else {
-            LBMD_FD_DISPATCH(L, return (launch_rows16<LBMD_BF16_SHIFTED, FDV, THV>(L, buf, ds, s)));
-        }
-    }
     const bool pairs = store != LBMD_F32 && L.nx % 2 == 0 &&
                        !(L.forcing == LBMD_FORCE_KOLMOGOROV && L.faxis == 0);
     if (pairs) {
@@ -680,6 +494,12 @@ cudaError_t launch_lb_fields(int store, const Lat &L, const void *cur, float *f,
                              DevState *ds, cudaStream_t s) {
     const dim3 b = node_block(L), g = node_grid(L, b);
     LBMD_DISPATCH(store, (k_lb_fields<SV><<<g, b, 0, s>>>(L, (const T *)cur, f, rho, u, ds)));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pull_f32(const Lat &L, const float *src, float *dst, cudaStream_t s) {
+    const dim3 b = node_block(L), g = node_grid(L, b);
+    k_pull_f32<<<g, b, 0, s>>>(L, src, dst);
     return cudaGetLastError();
 }
 

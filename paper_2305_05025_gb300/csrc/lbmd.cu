@@ -43,6 +43,9 @@ struct lbmd_s {
     lbmd_params p{};
     double kT = 0.0;          // thermal noise (lbmd_set_thermal)
     uint64_t seed = 0;
+    float *charge = nullptr;  // device charges (lbmd_set_charges)
+    float4 *unode = nullptr;  // node velocities of the step (lbmd_set_reinterpolation)
+    Lat *lat_dev = nullptr;   // device copy of L for the substeps (re-interpolation), set with each graph
     cudaStream_t stream = nullptr;            // caller's stream
     cudaStream_t s_main = nullptr, s_lat = nullptr;
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_t0 = nullptr, ev_t1 = nullptr;
@@ -264,6 +267,10 @@ void fill_physics(lbmd_t h) {
         A.binv_h[d] = (float)(A.bnc[d] / (double)Ls[d]);
     }
     A.bcap = fine ? kCapFine : kCap;
+    A.nl[0] = p.nx;
+    A.nl[1] = p.ny;
+    A.nl[2] = p.nz;
+    A.walls = p.walls_z;
     h->C.L = L;
     h->C.na = h->na;
 }
@@ -301,6 +308,10 @@ lbmd_status enqueue_step(lbmd_t h) {
 
 lbmd_status build_graph(lbmd_t h) {
     destroy_graph(h);
+    if (h->lat_dev) {  // every setter that changes L rebuilds the graph
+        CK(h, cudaMemcpyAsync(h->lat_dev, &h->L, sizeof(Lat), cudaMemcpyHostToDevice, h->stream));
+        CK(h, cudaStreamSynchronize(h->stream));
+    }
     CK(h, cudaStreamBeginCapture(h->s_main, cudaStreamCaptureModeThreadLocal));
     lbmd_status s = enqueue_step(h);
     cudaGraph_t g = nullptr;
@@ -341,8 +352,6 @@ lbmd_status read_flags(lbmd_t h) {
     if (flags & FLAG_NONFINITE) return fail(h, LBMD_ERR_NONFINITE, "non-finite value in the lattice or the atoms");
     if (flags & FLAG_CELL)
         return fail(h, LBMD_ERR_CELL, "a pair-search bucket overflowed: forces of a step missed pairs");
-    if (flags & FLAG_TIMEOUT)
-        return fail(h, LBMD_ERR_CUDA, "a lattice kernel gave up waiting for its bulk copies (bounded wait expired)");
     if (flags & FLAG_WALL) return fail(h, LBMD_ERR_STATE, "an atom's interpolation stencil crossed a z wall");
     return fail(h, LBMD_ERR_STATE, "touched-node list overflowed");
 }
@@ -920,6 +929,72 @@ lbmd_status lbmd_set_physics(lbmd_t h, double gamma, double tau, double force_am
     return LBMD_OK;
 }
 
+lbmd_status lbmd_set_charges(lbmd_t h, const double *charge, double coul_c, double coul_rc) {
+    if (!h) return fail(nullptr, LBMD_ERR_ARG, "handle is NULL");
+    AtomArgs &A = h->A;
+    if (h->state_set)
+        return fail(h, LBMD_ERR_STATE, "set the charges before lbmd_set_state (it computes the forces with them)");
+    if (!charge) {
+        A.coul = 0;
+        A.q = nullptr;
+        destroy_graph(h);
+        return LBMD_OK;
+    }
+    if (h->na == 0) return fail(h, LBMD_ERR_ARG, "charges need atoms (n_atoms > 0)");
+    const double rc = h->p.lj_sigma * h->p.lj_rcut_over_sigma;
+    if (!(coul_rc > 0.0) || coul_rc > rc)
+        return fail(h, LBMD_ERR_ARG, "coul_rc must be > 0 and <= the Lennard-Jones cutoff (the same pair lists)");
+    if (!std::isfinite(coul_c)) return fail(h, LBMD_ERR_ARG, "coul_c must be finite");
+    std::vector<float> q(h->na);
+    for (int a = 0; a < h->na; ++a) {
+        if (!std::isfinite(charge[a])) return fail(h, LBMD_ERR_ARG, "charges must be finite");
+        q[a] = (float)charge[a];
+    }
+    if (!h->charge) TRY(dalloc_t(h, &h->charge, (size_t)h->na));
+    CK(h, cudaMemcpyAsync(h->charge, q.data(), h->na * sizeof(float), cudaMemcpyHostToDevice, h->stream));
+    CK(h, cudaStreamSynchronize(h->stream));
+    A.q = h->charge;
+    A.coul = 1;
+    A.coul_2c = (float)(2.0 * coul_c);
+    A.coul_rc2 = (float)(coul_rc * coul_rc);
+    A.coul_irc3 = (float)(1.0 / (coul_rc * coul_rc * coul_rc));
+    destroy_graph(h);
+    return LBMD_OK;
+}
+
+lbmd_status lbmd_set_reinterpolation(lbmd_t h, int on) {
+    if (!h) return fail(nullptr, LBMD_ERR_ARG, "handle is NULL");
+    if (on != 0 && on != 1) return fail(h, LBMD_ERR_ARG, "on must be 0 or 1");
+    if (on && h->na == 0) return fail(h, LBMD_ERR_ARG, "re-interpolation needs atoms (n_atoms > 0)");
+    AtomArgs &A = h->A;
+    CouplingArgs &C = h->C;
+    if (on) {
+        if (!h->unode) TRY(dalloc_t(h, &h->unode, h->L.N));
+        // Each atom may claim its stencil and one node of margin (4 x 4 x 4).
+        const int cap = 64 * h->na;
+        if (C.touched_cap < cap) {
+            int *t = nullptr;
+            TRY(dalloc_t(h, &t, (size_t)cap));
+            C.touched = t;
+            C.touched_cap = cap;
+            h->fix_grid = (cap + 255) / 256;
+        }
+    }
+    A.reinterp = C.reinterp = on;
+    A.unode = C.unode = h->unode;
+    A.G = C.G;
+    if (on && !h->lat_dev) TRY(dalloc_t(h, &h->lat_dev, 1));
+    A.lat = h->lat_dev;
+    A.store = h->p.store;
+    A.pop[0] = h->pop[0];
+    A.pop[1] = h->pop[1];
+    A.tag = C.tag;
+    A.touched = C.touched;
+    A.touched_cap = C.touched_cap;
+    destroy_graph(h);
+    return LBMD_OK;
+}
+
 lbmd_status lbmd_set_thermal(lbmd_t h, double kT, uint64_t seed) {
     if (!h) return fail(nullptr, LBMD_ERR_ARG, "handle is NULL");
     if (!(kT >= 0.0) || !std::isfinite(kT)) return fail(h, LBMD_ERR_ARG, "kT must be finite and >= 0");
@@ -957,8 +1032,15 @@ lbmd_status lbmd_set_md_timing_events(lbmd_t h, void *ev_start, void *ev_stop) {
     return LBMD_OK;
 }
 
-lbmd_status lbmd_backward(lbmd_t h, int n_steps, int ckpt_every, int observable, double *d_gamma, double *d_tau,
-                          double *d_force_amp, double *obs) {
+}  // extern "C"
+
+namespace {
+
+// The rollout and reverse sweep of lbmd_backward; with grad_* given, also the
+// adjoint of the initial state in the ABI's terms.
+lbmd_status backward_impl(lbmd_t h, int n_steps, int ckpt_every, int observable, double *d_gamma, double *d_tau,
+                          double *d_force_amp, double *obs, float *grad_f, float *grad_x, float *grad_v,
+                          int on_device) {
     if (!h) return fail(nullptr, LBMD_ERR_ARG, "handle is NULL");
     if (!h->state_set) return fail(h, LBMD_ERR_STATE, "lbmd_set_state has not been called");
     if (n_steps < 1 || ckpt_every < 1) return fail(h, LBMD_ERR_ARG, "need n_steps >= 1 and ckpt_every >= 1");
@@ -966,6 +1048,8 @@ lbmd_status lbmd_backward(lbmd_t h, int n_steps, int ckpt_every, int observable,
     if (h->na == 0) return fail(h, LBMD_ERR_ARG, "the observables need atoms (n_atoms > 0)");
     if (h->kT > 0.0)
         return fail(h, LBMD_ERR_ARG, "the adjoint differentiates the deterministic step: set kT = 0 (lbmd_set_thermal)");
+    if (h->A.reinterp)
+        return fail(h, LBMD_ERR_ARG, "the adjoint covers the frozen-velocity coupling: turn re-interpolation off");
     TRY(adj_prepare(h, n_steps, ckpt_every));
     cudaStream_t s = h->stream;
     const int K = ckpt_every, nseg = (n_steps + K - 1) / K;
@@ -1034,6 +1118,29 @@ lbmd_status lbmd_backward(lbmd_t h, int n_steps, int ckpt_every, int observable,
             cur ^= 1;
         }
     }
+    // Adjoint of the initial state. The ABI's populations are the pull of the
+    // stored ones (f_i(x) = h_i(x - c_i)), so their adjoint is the pull of the
+    // storage adjoint; positions and velocities are the atoms' adjoints.
+    if (grad_f || grad_x || grad_v) {
+        const size_t nf = N * Q;
+        float *gf = grad_f, *gx = grad_x, *gv = grad_v;
+        void *p = nullptr;
+        if (!on_device) {
+            CK(h, stage(h, (nf + 2 * na3) * sizeof(float), &p));
+            gf = grad_f ? (float *)p : nullptr;
+            gx = grad_x ? (float *)p + nf : nullptr;
+            gv = grad_v ? (float *)p + nf + na3 : nullptr;
+        }
+        if (gf) CK(h, launch_pull_f32(h->L, h->hat[cur], gf, s));
+        if (gx) CK(h, cudaMemcpyAsync(gx, D.xhat, na3 * sizeof(float), cudaMemcpyDeviceToDevice, s));
+        if (gv) CK(h, cudaMemcpyAsync(gv, D.vhat, na3 * sizeof(float), cudaMemcpyDeviceToDevice, s));
+        if (!on_device) {
+            if (grad_f) CK(h, cudaMemcpyAsync(grad_f, gf, nf * sizeof(float), cudaMemcpyDeviceToHost, s));
+            if (grad_x) CK(h, cudaMemcpyAsync(grad_x, gx, na3 * sizeof(float), cudaMemcpyDeviceToHost, s));
+            if (grad_v) CK(h, cudaMemcpyAsync(grad_v, gv, na3 * sizeof(float), cudaMemcpyDeviceToHost, s));
+            CK(h, cudaStreamSynchronize(s));
+        }
+    }
     // Parameter gradients: d/d gamma from the atoms, d/d omega and d/d A from
     // the lattice (block partials plus touched-node corrections).
     CK(h, launch_sum_double(D.gam_acc, na, h->obs_acc + 1, s));
@@ -1053,6 +1160,22 @@ lbmd_status lbmd_backward(lbmd_t h, int n_steps, int ckpt_every, int observable,
     if (d_tau) *d_tau = -omh * om * om;
     if (d_force_amp) *d_force_amp = res[2] + corr[1];
     return LBMD_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+lbmd_status lbmd_backward(lbmd_t h, int n_steps, int ckpt_every, int observable, double *d_gamma, double *d_tau,
+                          double *d_force_amp, double *obs) {
+    return backward_impl(h, n_steps, ckpt_every, observable, d_gamma, d_tau, d_force_amp, obs, nullptr, nullptr,
+                         nullptr, 0);
+}
+
+lbmd_status lbmd_backward_state(lbmd_t h, int n_steps, int ckpt_every, int observable, double *obs, float *grad_f,
+                                float *grad_x, float *grad_v, int on_device) {
+    return backward_impl(h, n_steps, ckpt_every, observable, nullptr, nullptr, nullptr, obs, grad_f, grad_x, grad_v,
+                         on_device);
 }
 
 lbmd_status lbmd_analysis_begin(lbmd_t h, int n_sel, const int32_t *sel, const double *x_ref, int max_frames) {

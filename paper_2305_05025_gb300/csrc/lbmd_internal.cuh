@@ -39,7 +39,7 @@ __host__ __device__ __forceinline__ constexpr float wgt(int i) {
 }
 
 // Device error flags (bit mask), raised with atomicOr, read by the host.
-enum : int { FLAG_NONFINITE = 1, FLAG_CELL = 2, FLAG_WALL = 4, FLAG_TOUCHED = 8, FLAG_TIMEOUT = 16 };
+enum : int { FLAG_NONFINITE = 1, FLAG_CELL = 2, FLAG_WALL = 4, FLAG_TOUCHED = 8 };
 
 // Device-resident step state, updated by the last kernel of each step.
 struct DevState {
@@ -517,7 +517,7 @@ struct AtomArgs {
     float off[3];         // step-frame origin per axis (exact in FP32)
     double offd[3];
     double *X;            // 3*na FP64 accumulator
-    float4 *P[2];         // (hi x, hi y, hi z, 0) by substep parity
+    float4 *P[2];         // (hi x, hi y, hi z, charge) by substep parity
     float4 *L[2];         // (lo x, lo y, lo z, 0) by substep parity
     float *P0, *R0;       // 3*na step-start hi and lo parts
     float *V, *F, *U, *J; // 3*na SoA each
@@ -533,6 +533,26 @@ struct AtomArgs {
     int *nnb;             // list lengths
     float *D;             // 3*na drift since the last list build
     float rl2;            // (rc + skin)^2, list radius squared
+    // Screened Coulomb pairs (charge in the w component of P): pair force
+    // 2 C q_a q_b (r^-4 - rcc^-3 r^-1) d within rcc <= rc; coul = 0: off.
+    int coul;
+    float coul_2c, coul_rc2, coul_irc3;
+    const float *q;       // na charges (by atom), or NULL
+    // Re-interpolated coupling: every substep kernel interpolates U at x_k
+    // from the step's node velocities and spreads its own friction impulse.
+    int reinterp;
+    const float4 *unode;  // node velocities of the step (w: the step's stamp), from the interpolation
+    float4 *G;            // per node coupling force (the spread's target)
+    int nl[3];            // lattice nodes per axis
+    int walls;
+    // Nodes outside the region the interpolation froze (an atom that moved
+    // more than one node within the step): their velocities come from the
+    // step's populations, and they join the touched-node list.
+    const Lat *lat;          // device copy of the lattice description
+    int store;               // LBMD_F32 / LBMD_F16_SHIFTED / LBMD_BF16_SHIFTED
+    const void *pop[2];      // population buffers; the step reads pop[step & 1]
+    int *tag, *touched;      // touched-node stamps and list (as the interpolation's)
+    int touched_cap;
     float half_skin2;     // (skin/2)^2, drift that triggers a rebuild
     int *scan_local;      // Morton-code exclusive scan within blocks of 1024
     int *scan_block;      // kMortonCodes / 1024 block offsets
@@ -556,7 +576,7 @@ __device__ __forceinline__ bool set_frame(const AtomArgs &A, int a, float4 &p, f
         A.P0[d * A.na + a] = hi[d];
         A.R0[d * A.na + a] = lo[d];
     }
-    p = make_float4(hi[0], hi[1], hi[2], 0.f);
+    p = make_float4(hi[0], hi[1], hi[2], A.q ? A.q[a] : 0.f);  // w: the atom's charge
     l = make_float4(lo[0], lo[1], lo[2], 0.f);
     return finite;
 }
@@ -573,6 +593,8 @@ struct CouplingArgs {
     int touched_cap;
     float4 *G;      // per node coupling force (x, y, z, unused)
     const int *order;  // atoms in warp-sorted (Morton bucket) order, as AtomArgs::order
+    int reinterp;      // 1: the substeps interpolate and spread (see AtomArgs)
+    float4 *unode;     // node velocities of the step's region (re-interpolation only)
     DevState *ds;
     int keep;       // 1: the fix-up leaves G and the touched list for the adjoint
 };
@@ -626,6 +648,7 @@ cudaError_t launch_lb_fields(int store, const Lat &L, const void *cur, float *f,
                              DevState *ds, cudaStream_t s);
 cudaError_t launch_lb_init(int store, const Lat &L, void *dst, const float *f, const float *rho, const float *u,
                            cudaStream_t s);
+cudaError_t launch_pull_f32(const Lat &L, const float *src, float *dst, cudaStream_t s);
 cudaError_t launch_lb_reduce(int store, const Lat &L, const void *cur, double *partials, int nblocks, DevState *ds,
                              cudaStream_t s);
 cudaError_t launch_reduce_finish(const double *partials, int nblocks, int width, double *out, cudaStream_t s);

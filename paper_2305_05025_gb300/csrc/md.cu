@@ -207,7 +207,9 @@ __device__ void md_force_warp(const AtomArgs &A, const float4 *__restrict__ P, c
         const float inv_r2 = 1.0f / r2;
         const float sr2 = A.lj_sig2 * inv_r2;
         const float sr6 = sr2 * sr2 * sr2;
-        const float fr = A.lj_24eps * inv_r2 * sr6 * (2.f * sr6 - 1.f) - A.lj_fc * rsqrtf(r2);
+        float fr = A.lj_24eps * inv_r2 * sr6 * (2.f * sr6 - 1.f) - A.lj_fc * rsqrtf(r2);
+        if (A.coul && r2 < A.coul_rc2)
+            fr += A.coul_2c * pa.w * P[q].w * (inv_r2 * inv_r2 - A.coul_irc3 * rsqrtf(r2));
         fx += fr * d[0];
         fy += fr * d[1];
         fz += fr * d[2];
@@ -520,7 +522,10 @@ __device__ __forceinline__ void list_force(const AtomArgs &A, const float4 *__re
                 const float inv_r2 = 1.0f / r2;
                 const float sr2 = A.lj_sig2 * inv_r2;
                 const float sr6 = sr2 * sr2 * sr2;
-                const float fr = A.lj_24eps * inv_r2 * sr6 * (2.f * sr6 - 1.f) - A.lj_fc * rsqrtf(r2);
+                const float ir = rsqrtf(r2);
+                float fr = A.lj_24eps * inv_r2 * sr6 * (2.f * sr6 - 1.f) - A.lj_fc * ir;
+                if (A.coul && r2 < A.coul_rc2)
+                    fr += A.coul_2c * pa.w * ph[u].w * (inv_r2 * inv_r2 - A.coul_irc3 * ir);
                 fx += fr * d[0];
                 fy += fr * d[1];
                 fz += fr * d[2];
@@ -571,7 +576,41 @@ __device__ __forceinline__ float4 shfl4(float4 v, int src) {
 // 20k-atom grid fits one wave); 4 lanes at 10 blocks (48 registers): 8%
 // faster than 8 blocks at 64 registers on 200k atoms, where the grid takes
 // several waves and more resident warps hide more latency.
-template <int TPA, int NB, int W>
+// Component d of the velocity (sum f c + g/2)/rho of node (x, y, z) from the
+// populations pulled into it: the value the interpolation computes for its
+// nodes, with two running sums instead of the 19 pulled values.
+template <int S>
+__device__ __forceinline__ float pulled_velocity(const typename Store<S>::T *__restrict__ src, const Lat &L, int x,
+                                                 int y, int z, int d) {
+    const int xm = x == 0 ? L.nx - 1 : x - 1, xp = x == L.nx - 1 ? 0 : x + 1;
+    const int ym = y == 0 ? L.ny - 1 : y - 1, yp = y == L.ny - 1 ? 0 : y + 1;
+    const int zm = z == 0 ? L.nz - 1 : z - 1, zp = z == L.nz - 1 ? 0 : z + 1;
+    const size_t node = ((size_t)z * L.ny + y) * L.nx + x;
+    float drho = 0.f, j = 0.f;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        const float f = Store<S>::ld(src + pull_index(L, i, x, y, z, xm, xp, ym, yp, zm, zp, node));
+        drho += f;
+        if (d == 0 && cx(i)) j += cx(i) * f;
+        if (d == 1 && cy(i)) j += cy(i) * f;
+        if (d == 2 && cz(i)) j += cz(i) * f;
+    }
+    float g[3];
+    body_force(L, x, y, z, g);
+    const float inv = 1.f / (L.rho0 + drho);
+    return (j + 0.5f * g[d]) * inv;
+}
+
+// The same for any storage format; out of line, so that the registers it
+// needs are saved only on this rare path and not reserved in the substep.
+__device__ __noinline__ float far_velocity(const void *src, int store, const Lat *Lp, int x, int y, int z, int d) {
+    const Lat &L = *Lp;
+    if (store == LBMD_F32) return pulled_velocity<LBMD_F32>((const float *)src, L, x, y, z, d);
+    if (store == LBMD_F16_SHIFTED) return pulled_velocity<LBMD_F16_SHIFTED>((const __half *)src, L, x, y, z, d);
+    return pulled_velocity<LBMD_BF16_SHIFTED>((const __nv_bfloat16 *)src, L, x, y, z, d);
+}
+
+template <int TPA, int NB, int W, bool RI>
 __global__ void __launch_bounds__(128, TPA == 8 ? 9 : 10) k_md_substep(AtomArgs A, int k) {
     const int lane = threadIdx.x & 31;
     const int sub = lane & (TPA - 1);
@@ -642,18 +681,92 @@ __global__ void __launch_bounds__(128, TPA == 8 ? 9 : 10) k_md_substep(AtomArgs 
         list_force<TPA, NB>(A, A.P[par], A.L[par], a, pa, la, sub, nlist, b0, b1, F);
     }
     if (!valid) return;
+    // Re-interpolated coupling: U at x_k from the step's node velocities
+    // (lanes 0-2, one component each), the trilinear stencil of x_k kept for
+    // the spread of this kernel's impulse below.
+    float Uk = Ud, wt[3] = {0.f, 0.f, 0.f};
+    int bcell[3] = {0, 0, 0};
+    if (RI && sub < 3) {
+        const float hi4[3] = {pa.x, pa.y, pa.z}, lo4[3] = {la.x, la.y, la.z};
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            const float s0 = hi4[d] - A.off[d];  // exact: both in the step frame's binade
+            float fl = floorf(s0);
+            float t = (s0 - fl) + lo4[d];
+            if (t < 0.f) {
+                t += 1.f;
+                fl -= 1.f;
+            } else if (t >= 1.f) {
+                t -= 1.f;
+                fl += 1.f;
+            }
+            wt[d] = t;
+            int c = (int)fl;
+            if (d == 2 && A.walls) {
+                if (c < 0 || c + 1 > A.nl[2] - 1) {
+                    atomicOr(&A.ds->flags, FLAG_WALL);
+                    c = c < 0 ? 0 : A.nl[2] - 2;
+                }
+            } else {
+                c = wrapi(c, A.nl[d]);
+            }
+            bcell[d] = c;
+        }
+        const int stamp = step + 1;
+        float u = 0.f;
+        unsigned far = 0;  // corners outside the frozen region
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            const int o[3] = {j & 1, (j >> 1) & 1, (j >> 2) & 1};
+            const int xx = o[0] ? (bcell[0] + 1 == A.nl[0] ? 0 : bcell[0] + 1) : bcell[0];
+            const int yy = o[1] ? (bcell[1] + 1 == A.nl[1] ? 0 : bcell[1] + 1) : bcell[1];
+            const int zz = o[2] ? (bcell[2] + 1 == A.nl[2] ? 0 : bcell[2] + 1) : bcell[2];
+            const float W = (o[0] ? wt[0] : 1.f - wt[0]) * (o[1] ? wt[1] : 1.f - wt[1]) * (o[2] ? wt[2] : 1.f - wt[2]);
+            const float4 un = A.unode[((size_t)zz * A.nl[1] + yy) * A.nl[0] + xx];
+            if (__float_as_int(un.w) == stamp)
+                u += W * (sub == 0 ? un.x : (sub == 1 ? un.y : un.z));
+            else
+                far |= 1u << j;
+        }
+        // An atom that moved more than one node from its step-start stencil
+        // within the step: the velocity of a corner the interpolation did not
+        // freeze comes from the step's populations (which no kernel writes
+        // during the substeps), the same value the interpolation would have
+        // stored, and the node joins the step's touched list so that the
+        // impulse spread onto it reaches the collision.
+#pragma unroll 1
+        for (int j = 0; far; ++j) {
+            if (!(far >> j & 1u)) continue;
+            far &= ~(1u << j);
+            const int o[3] = {j & 1, (j >> 1) & 1, (j >> 2) & 1};
+            const int xx = o[0] ? (bcell[0] + 1 == A.nl[0] ? 0 : bcell[0] + 1) : bcell[0];
+            const int yy = o[1] ? (bcell[1] + 1 == A.nl[1] ? 0 : bcell[1] + 1) : bcell[1];
+            const int zz = o[2] ? (bcell[2] + 1 == A.nl[2] ? 0 : bcell[2] + 1) : bcell[2];
+            const float W = (o[0] ? wt[0] : 1.f - wt[0]) * (o[1] ? wt[1] : 1.f - wt[1]) * (o[2] ? wt[2] : 1.f - wt[2]);
+            u += W * far_velocity(A.pop[step & 1], A.store, A.lat, xx, yy, zz, sub);
+            const int node = (int)(((size_t)zz * A.nl[1] + yy) * A.nl[0] + xx);
+            if (sub == 0 && A.tag[node] != stamp && atomicExch(&A.tag[node], stamp) != stamp) {
+                const int t = atomicAdd(&A.ds->n_touched, 1);
+                if (t < A.touched_cap)
+                    A.touched[t] = node;
+                else
+                    atomicOr(&A.ds->flags, FLAG_TOUCHED);
+            }
+        }
+        Uk = u;
+    }
     // Lanes 0-2: one velocity-Verlet component each.
     float v = vd, J = Jd, p = 0.f, lo = 0.f, Dd = 0.f;
     const float Fd = sub == 0 ? F[0] : (sub == 1 ? F[1] : F[2]);
     if (A.recF && sub < 3) A.recF[(size_t)k * 3 * na + sub * na + a] = Fd;
     if (sub < 3) {
         if (k > 0) {  // second half-kick of substep k-1, drag at v_{k-1/2}
-            const float drag = A.gamma * (Ud - v);
+            const float drag = A.gamma * (Uk - v);
             J += A.hdt * drag;
             v += A.hdt * (Fd + drag) * im;
         }
         if (k < A.n_md) {  // first half-kick of substep k, drag at v_k, then drift
-            const float drag = A.gamma * (Ud - v);
+            const float drag = A.gamma * (Uk - v);
             J += A.hdt * drag;
             v += A.hdt * (Fd + drag) * im;
             p = sub == 0 ? pa.x : (sub == 1 ? pa.y : pa.z);
@@ -682,15 +795,34 @@ __global__ void __launch_bounds__(128, TPA == 8 ? 9 : 10) k_md_substep(AtomArgs 
         A.V[sub * na + a] = v;
         A.J[sub * na + a] = J;
     }
-    if (k == A.n_md) return;
     const int base = lane & ~(TPA - 1);
     const unsigned gm = (TPA == 32 ? 0xffffffffu : ((1u << TPA) - 1u)) << base;  // valid groups are whole
+    if (RI) {
+        // The fluid receives the opposite of this kernel's friction impulse,
+        // with the weights U was interpolated with.
+        const float dJ = sub < 3 ? J - Jd : 0.f;
+        const float jx = __shfl_sync(gm, dJ, base), jy = __shfl_sync(gm, dJ, base + 1),
+                    jz = __shfl_sync(gm, dJ, base + 2);
+        if (sub == 0) {
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                const int o[3] = {j & 1, (j >> 1) & 1, (j >> 2) & 1};
+                const int xx = o[0] ? (bcell[0] + 1 == A.nl[0] ? 0 : bcell[0] + 1) : bcell[0];
+                const int yy = o[1] ? (bcell[1] + 1 == A.nl[1] ? 0 : bcell[1] + 1) : bcell[1];
+                const int zz = o[2] ? (bcell[2] + 1 == A.nl[2] ? 0 : bcell[2] + 1) : bcell[2];
+                const float W =
+                    (o[0] ? wt[0] : 1.f - wt[0]) * (o[1] ? wt[1] : 1.f - wt[1]) * (o[2] ? wt[2] : 1.f - wt[2]);
+                atomicAdd(&A.G[((size_t)zz * A.nl[1] + yy) * A.nl[0] + xx], make_float4(-W * jx, -W * jy, -W * jz, 0.f));
+            }
+        }
+    }
+    if (k == A.n_md) return;
     const float px = __shfl_sync(gm, p, base), py = __shfl_sync(gm, p, base + 1), pz = __shfl_sync(gm, p, base + 2);
     const float lx = __shfl_sync(gm, lo, base), ly = __shfl_sync(gm, lo, base + 1), lz = __shfl_sync(gm, lo, base + 2);
     const float D2 = __shfl_sync(gm, Dd * Dd, base) + __shfl_sync(gm, Dd * Dd, base + 1) +
                      __shfl_sync(gm, Dd * Dd, base + 2);
     if (sub != 0) return;
-    const float4 pn = make_float4(px, py, pz, 0.f), ln = make_float4(lx, ly, lz, 0.f);
+    const float4 pn = make_float4(px, py, pz, pa.w), ln = make_float4(lx, ly, lz, 0.f);  // w: charge
     A.P[par ^ 1][a] = pn;
     A.L[par ^ 1][a] = ln;
     A.count[gp3][old_bucket] = 0;
@@ -777,7 +909,7 @@ cudaError_t launch_md_prime(const AtomArgs &a, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-template <int TPA, int W>
+template <int TPA, int W, bool RI>
 cudaError_t launch_substep(const AtomArgs &a, int k, cudaStream_t s) {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((a.na + 4 * (32 / TPA) - 1) / (4 * (32 / TPA)));  // 128 threads, TPA lanes per atom
@@ -788,14 +920,19 @@ cudaError_t launch_substep(const AtomArgs &a, int k, cudaStream_t s) {
     attr[0].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, k_md_substep<TPA, 2, W>, a, k);
+    return cudaLaunchKernelEx(&cfg, k_md_substep<TPA, 2, W, RI>, a, k);
 }
 
 cudaError_t launch_md_substep(const AtomArgs &a, int k, cudaStream_t s) {
     if (a.na == 0) return cudaSuccess;
     // Above ~64k atoms the 8-lane grid no longer fits the GPU in one wave.
-    if (a.bwin == 5) return a.na > 65536 ? launch_substep<4, 5>(a, k, s) : launch_substep<8, 5>(a, k, s);
-    return a.na > 65536 ? launch_substep<4, 3>(a, k, s) : launch_substep<8, 3>(a, k, s);
+    if (a.reinterp) {
+        if (a.bwin == 5)
+            return a.na > 65536 ? launch_substep<4, 5, true>(a, k, s) : launch_substep<8, 5, true>(a, k, s);
+        return a.na > 65536 ? launch_substep<4, 3, true>(a, k, s) : launch_substep<8, 3, true>(a, k, s);
+    }
+    if (a.bwin == 5) return a.na > 65536 ? launch_substep<4, 5, false>(a, k, s) : launch_substep<8, 5, false>(a, k, s);
+    return a.na > 65536 ? launch_substep<4, 3, false>(a, k, s) : launch_substep<8, 3, false>(a, k, s);
 }
 
 cudaError_t launch_md_sort(const AtomArgs &a, cudaStream_t s) {

@@ -80,17 +80,21 @@ def lib():
         L.lbmd_set_timing_events.argtypes = [vp, vp, vp]
         L.lbmd_set_md_timing_events.argtypes = [vp, vp, vp]
         L.lbmd_set_thermal.argtypes = [vp, C.c_double, C.c_uint64]
+        L.lbmd_set_charges.argtypes = [vp, vp, C.c_double, C.c_double]
+        L.lbmd_set_reinterpolation.argtypes = [vp, ip]
         L.lbmd_analysis_begin.argtypes = [vp, ip, vp, vp, ip]
         L.lbmd_analysis_frame.argtypes = [vp, dp, dp]
         L.lbmd_analysis_result.argtypes = [vp, vp, vp, vp, ip]
         L.lbmd_backward.argtypes = [vp, ip, ip, ip, dp, dp, dp, dp]
+        L.lbmd_backward_state.argtypes = [vp, ip, ip, ip, dp, vp, vp, vp, ip]
         L.lbmd_last_error.argtypes = [vp]
         L.lbmd_last_error.restype = C.c_char_p
         L.lbmd_destroy.argtypes = [vp]
         L.lbmd_destroy.restype = None
         for name in ("lbmd_create", "lbmd_set_state", "lbmd_step", "lbmd_get_fields", "lbmd_get_stats",
                      "lbmd_check", "lbmd_cell_list", "lbmd_set_physics", "lbmd_set_timing_events", "lbmd_set_md_timing_events",
-                     "lbmd_analysis_begin", "lbmd_analysis_frame", "lbmd_analysis_result", "lbmd_set_thermal",
+                     "lbmd_analysis_begin", "lbmd_analysis_frame", "lbmd_analysis_result", "lbmd_set_thermal", "lbmd_set_charges",
+                     "lbmd_set_reinterpolation", "lbmd_backward_state",
                      "lbmd_backward", "lbmd_version"):
             getattr(L, name).restype = C.c_int
         _lib = L
@@ -259,6 +263,19 @@ def lbmd_set_physics(h, gamma, tau, force_amp):
     h.params.gamma, h.params.tau, h.params.force_amp = float(gamma), float(tau), float(force_amp)
 
 
+def lbmd_set_charges(h, charge, coul_c=0.0, coul_rc=1.0):
+    """Screened Coulomb pairs (see include/lbmd.h); charge None turns them off.
+    Call before lbmd_set_state."""
+    keep = []
+    p, _ = (None, None) if charge is None else _ptr(np.asarray(charge, np.float64), np.float64, (h.n_atoms,), keep)
+    _check(h, lib().lbmd_set_charges(h, p, float(coul_c), float(coul_rc)))
+
+
+def lbmd_set_reinterpolation(h, on=True):
+    """Fluid velocity re-interpolated at every substep (see include/lbmd.h)."""
+    _check(h, lib().lbmd_set_reinterpolation(h, int(bool(on))))
+
+
 def lbmd_set_thermal(h, kT, seed=0):
     """Thermal noise of the fluid: kT > 0 turns it on (see include/lbmd.h)."""
     _check(h, lib().lbmd_set_thermal(h, float(kT), int(seed) & 0xFFFFFFFFFFFFFFFF))
@@ -319,6 +336,18 @@ def lbmd_analysis_result(h, cov=True):
     p = lambda a: None if a is None else a.ctypes.data_as(C.c_void_p)
     _check(h, lib().lbmd_analysis_result(h, p(mean), p(rmsf), p(c), 0))
     return mean, rmsf, c
+
+
+def lbmd_backward_state(h, n_steps, ckpt_every, observable=OBS_DRAG_X):
+    """Returns (observable, d obs/d f0 (19, N), d obs/d x0 (3, n), d obs/d v0 (3, n))."""
+    obs = C.c_double()
+    gf = np.zeros((Q, h.N), np.float32)
+    gx = np.zeros((3, h.n_atoms), np.float32)
+    gv = np.zeros((3, h.n_atoms), np.float32)
+    p = lambda a: a.ctypes.data_as(C.c_void_p)
+    _check(h, lib().lbmd_backward_state(h, int(n_steps), int(ckpt_every), int(observable), C.byref(obs), p(gf),
+                                        p(gx), p(gv), 0))
+    return obs.value, gf, gx, gv
 
 
 def lbmd_destroy(h):

@@ -16,9 +16,18 @@ def rel_linf(a, b):
 
 def make(cfg, inp):
     h = lbmd.lbmd_create(cfg, inp["mass"], inp["bonds"], inp["bond_k"], inp["bond_r0"])
+    if inp.get("charge") is not None:
+        lbmd.lbmd_set_charges(h, inp["charge"], cfg["coul_c"], cfg["coul_rc"])
+    if cfg.get("reinterp"):
+        lbmd.lbmd_set_reinterpolation(h, True)
     lbmd.lbmd_set_state(h, rho=inp["rho"].astype(np.float32), u=inp["u"].astype(np.float32),
                         x=inp["x"], v=inp["v"].astype(np.float32))
     return h
+
+
+def topology(orc, inp):
+    """The oracle's topology of the inputs (with their charges, if any)."""
+    return orc.Topology(inp["mass"], inp["bonds"], inp["bond_k"], inp["bond_r0"], charge=inp.get("charge"))
 
 
 def oracle_start(orc, cfg, inp):
@@ -27,8 +36,7 @@ def oracle_start(orc, cfg, inp):
     rho = inp["rho"].astype(np.float32).astype(np.float64)
     u = inp["u"].astype(np.float32).astype(np.float64)
     f = orc.equilibrium(rho, u)
-    topo = orc.Topology(inp["mass"], inp["bonds"], inp["bond_k"], inp["bond_r0"])
-    return f, inp["x"].copy(), inp["v"].astype(np.float32).astype(np.float64), topo
+    return f, inp["x"].copy(), inp["v"].astype(np.float32).astype(np.float64), topology(orc, inp)
 
 
 def gpu_state(h):
@@ -52,21 +60,28 @@ def lattice_inputs(shape, sigma, seed, rho0=1.0):
 HALF_ULP = 2.0 ** -24
 
 
-def fp32_floor(orc, cfg, topo, f, x, v, steps, seed=0):
+def fp32_floor(orc, cfg, topo, f, x, v, steps, seed=0, draws=2):
     """Relative L-infinity response of the FP64 oracle, after `steps` steps, to
     perturbing its inputs at the resolution the CUDA path stores them with:
     delta f and v by one FP32 half-ulp (relative), positions by one half-ulp of
-    a unit cell offset (absolute). A CUDA result within this bound is as
-    accurate as an exact computation from FP32-rounded inputs."""
-    rng = np.random.default_rng(seed)
+    a unit cell offset (absolute); per field the largest response over
+    `draws` independent random perturbations (one draw can under-estimate the
+    sensitivity). A CUDA result within this bound is as accurate as an exact
+    computation from FP32-rounded inputs."""
     w = np.array([1 / 3] + [1 / 18] * 6 + [1 / 36] * 12)[:, None] * cfg.get("rho0", 1.0)
-    fp = w + (f - w) * (1 + rng.uniform(-HALF_ULP, HALF_ULP, f.shape))
-    xp = x + rng.uniform(-HALF_ULP, HALF_ULP, x.shape)
-    vp = v * (1 + rng.uniform(-HALF_ULP, HALF_ULP, v.shape))
     fa, xa, va, _ = orc.run(cfg, topo, f, x, v, steps)
-    fb, xb, vb, _ = orc.run(cfg, topo, fp, xp, vp, steps)
-    return dict(f=rel_linf(fb, fa), u=rel_linf(velocity(orc, cfg, fb), velocity(orc, cfg, fa)),
-                x=rel_linf(xb, xa), v=rel_linf(vb, va)), (fa, xa, va)
+    ua = velocity(orc, cfg, fa)
+    floors = dict(f=0.0, u=0.0, x=0.0, v=0.0)
+    for d in range(draws):
+        rng = np.random.default_rng(seed + 7919 * d)
+        fp = w + (f - w) * (1 + rng.uniform(-HALF_ULP, HALF_ULP, f.shape))
+        xp = x + rng.uniform(-HALF_ULP, HALF_ULP, x.shape)
+        vp = v * (1 + rng.uniform(-HALF_ULP, HALF_ULP, v.shape))
+        fb, xb, vb, _ = orc.run(cfg, topo, fp, xp, vp, steps)
+        resp = dict(f=rel_linf(fb, fa), u=rel_linf(velocity(orc, cfg, fb), ua), x=rel_linf(xb, xa),
+                    v=rel_linf(vb, va))
+        floors = {k: max(floors[k], resp[k]) for k in floors}
+    return floors, (fa, xa, va)
 
 
 def assert_within(errs, floors, tol=1e-5):
@@ -77,12 +92,14 @@ def assert_within(errs, floors, tol=1e-5):
 
 
 # Factor on the FP32 floor in the per-step bounds. The floor is the oracle's
-# response to ONE rounding of the step's inputs; the CUDA path also rounds
-# inside the step (velocities at every half-kick, pair forces at every
-# substep), yet over the suite's 604 per-field, per-step comparisons the
-# worst error / floor among those where the floor term binds (error > 1e-5)
-# was 1.09 (random-mass chain, v). FLOOR_FACTOR = 2 keeps that margin; the
-# errors did not need the sqrt(n_md) ~ 11 random-walk factor once assumed.
+# response to one rounding of the step's inputs (the larger of two random
+# draws); the CUDA path also rounds inside the step (velocities at every
+# half-kick, pair forces at every substep). Over the suite's per-field,
+# per-step comparisons the worst error / floor where the floor term binds
+# (error > 1e-5) was 1.09 in one run of 604 comparisons and 2.26 (chain500,
+# step 57, v) against a single-draw floor in a later run; with the
+# two-draw floor FLOOR_FACTOR = 2 keeps a margin without the sqrt(n_md) ~ 11
+# random-walk factor once assumed.
 FLOOR_FACTOR = 2.0
 
 
@@ -107,7 +124,7 @@ def teacher_forced(orc, cfg, inp, steps, name, h=None):
     the GPU's own next state and with the FP32 floor of that step. Returns the
     steps done and the worst error / floor_bound per field."""
     h = make(cfg, inp) if h is None else h
-    topo = orc.Topology(inp["mass"], inp["bonds"], inp["bond_k"], inp["bond_r0"])
+    topo = topology(orc, inp)
     worst = dict(f=0.0, u=0.0, x=0.0, v=0.0)
     s = lbmd.lbmd_get_fields(h, f=True, x=True, v=True)
     done = 0

@@ -27,7 +27,7 @@ def _cfg(**kw):
 
 @pytest.mark.parametrize("store", ["f32", "f16", "bf16"])
 @pytest.mark.parametrize("walls", [0, 1])
-@pytest.mark.parametrize("nx", [17, 66, 64])  # odd: one node per thread; even: node pairs; nx % 8 = 0: whole rows
+@pytest.mark.parametrize("nx", [17, 66, 64])  # odd: one node per thread; even: node pairs
 def test_rest_state_is_bit_exact(store, walls, nx):
     cfg = _cfg(store=store, walls_z=walls, nx=nx, ny=9, nz=6)
     inp = lattice_inputs((nx, 9, 6), 0.0, 1)
@@ -74,9 +74,7 @@ def test_walls_poiseuille_matches_oracle(orc):
 # on the same cases. Bounds: FP32 1e-5 on f and u; FP16 and BF16 their
 # storage resolution of delta f (2^-11 and 2^-8 relative) on delta f and u.
 @pytest.mark.parametrize("store,bound", [("f32", TOL), ("f16", 2e-3), ("bf16", 2e-2)])
-# 16-bit stores: nx = 70 runs the pair kernel (35 pairs: a partial warp),
-# nx = 96 the whole-row kernel (rows staged in shared memory by bulk copies).
-@pytest.mark.parametrize("nx", [70, 96])
+@pytest.mark.parametrize("nx", [70, 96])  # pair kernel: row of 35 pairs (partial warp) and of 48 (warp edge)
 def test_pair_kernel_matches_oracle(orc, nx, store, bound):
     cfg = _cfg(nx=nx, ny=5, nz=4, tau=0.7, walls_z=1, forcing="kolmogorov", force_amp=1e-4, force_wave_axis=2,
                store=store)
