@@ -192,9 +192,9 @@ lbmd_status lbmd_set_charges(lbmd_t h, const double *charge, double coul_c, doub
  * stencil and one node of margin; a substep that finds its atom beyond them
  * computes the missing ones from the step's populations, so any displacement
  * within a step is handled exactly. Costs one node-velocity array (16 bytes
- * per node) and a touched-node list of 64 entries per atom (LBMD_ERR_STATE if
- * the atoms claim more nodes in one step). The step graph is rebuilt on the
- * next lbmd_step; lbmd_backward refuses on = 1. */
+ * per node) and a touched-node list of min(N, 256 per atom) entries
+ * (LBMD_ERR_STATE if the atoms claim more nodes in one step). The step graph
+ * is rebuilt on the next lbmd_step; lbmd_backward refuses on = 1. */
 lbmd_status lbmd_set_reinterpolation(lbmd_t h, int on);
 
 /* Thermal fluctuations of the fluid (Sec. 2.2: the noise xi_i of the

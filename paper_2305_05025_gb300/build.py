@@ -12,7 +12,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "liblbmd.so")
-SOURCES = ["lbmd.cu", "lb.cu", "md.cu", "coupling.cu", "adjoint.cu", "noalloc.cu", "analysis.cu"]
+SOURCES = ["lbmd.cu", "lb.cu", "lb_step.cu", "md.cu", "coupling.cu", "adjoint.cu", "noalloc.cu", "analysis.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-Wall"]
 

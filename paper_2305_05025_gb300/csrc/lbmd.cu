@@ -26,6 +26,7 @@ namespace {
 
 thread_local std::string g_create_error;
 
+constexpr int kFixBlocks = 152 * 8;  // grid of the fix-up kernel (grid-stride over the touched nodes)
 constexpr int kFold = 128;  // bucket grid per axis (cells folded modulo this)
 // Atoms per bucket: a collapsed Lennard-Jones globule (sigma 0.4) packs ~30
 // atoms into a cell of side 1.3, and folding (cells 128 apart share a bucket
@@ -737,7 +738,7 @@ lbmd_status lbmd_create(const lbmd_params *params, int n_atoms, const double *ma
         C.J = A.J;
         C.order = A.order;
     }
-    h->fix_grid = na > 0 ? (C.touched_cap + 255) / 256 : 1;
+    h->fix_grid = na > 0 ? std::min((C.touched_cap + 255) / 256, kFixBlocks) : 1;
     CREATE_CK(cudaStreamSynchronize(h->stream));
     *out = h;
 #undef CREATE_TRY
@@ -970,14 +971,16 @@ lbmd_status lbmd_set_reinterpolation(lbmd_t h, int on) {
     CouplingArgs &C = h->C;
     if (on) {
         if (!h->unode) TRY(dalloc_t(h, &h->unode, h->L.N));
-        // Each atom may claim its stencil and one node of margin (4 x 4 x 4).
-        const int cap = 64 * h->na;
+        // Each atom claims its stencil and one node of margin (4 x 4 x 4),
+        // plus the nodes it reaches beyond them; a node enters once per step,
+        // so N entries always suffice.
+        const int cap = (int)std::min<size_t>(h->L.N, 256 * (size_t)h->na);
         if (C.touched_cap < cap) {
             int *t = nullptr;
             TRY(dalloc_t(h, &t, (size_t)cap));
             C.touched = t;
             C.touched_cap = cap;
-            h->fix_grid = (cap + 255) / 256;
+            h->fix_grid = std::min((cap + 255) / 256, kFixBlocks);
         }
     }
     A.reinterp = C.reinterp = on;

@@ -587,8 +587,8 @@ __device__ __forceinline__ float pulled_velocity(const typename Store<S>::T *__r
     const int zm = z == 0 ? L.nz - 1 : z - 1, zp = z == L.nz - 1 ? 0 : z + 1;
     const size_t node = ((size_t)z * L.ny + y) * L.nx + x;
     float drho = 0.f, j = 0.f;
-#pragma unroll
-    for (int i = 0; i < Q; ++i) {
+#pragma unroll 1
+    for (int i = 0; i < Q; ++i) {  // one population at a time: a rare path, kept small
         const float f = Store<S>::ld(src + pull_index(L, i, x, y, z, xm, xp, ym, yp, zm, zp, node));
         drho += f;
         if (d == 0 && cx(i)) j += cx(i) * f;
@@ -601,9 +601,8 @@ __device__ __forceinline__ float pulled_velocity(const typename Store<S>::T *__r
     return (j + 0.5f * g[d]) * inv;
 }
 
-// The same for any storage format; out of line, so that the registers it
-// needs are saved only on this rare path and not reserved in the substep.
-__device__ __noinline__ float far_velocity(const void *src, int store, const Lat *Lp, int x, int y, int z, int d) {
+// The same for any storage format.
+__device__ __forceinline__ float far_velocity(const void *src, int store, const Lat *Lp, int x, int y, int z, int d) {
     const Lat &L = *Lp;
     if (store == LBMD_F32) return pulled_velocity<LBMD_F32>((const float *)src, L, x, y, z, d);
     if (store == LBMD_F16_SHIFTED) return pulled_velocity<LBMD_F16_SHIFTED>((const __half *)src, L, x, y, z, d);
