@@ -461,7 +461,7 @@ def run_ours(args, cfg):
     lbmd.lbmd_destroy(h)
     del pin, outs
 
-    launches = (n_md + 8) if na > 0 else 2  # 3 sort + interp + (n_md + 1) substeps + spread + dense + fix-up
+    launches = (n_md + 9) if na > 0 else 2  # 4 sort + interp + (n_md + 1) substeps + spread + dense + fix-up
     lat_roof = {s: _lattice_roofline(s, nodes, runs[s]["lb_ms"], hbm, peak_kind) for s in stores}
     # The dominant kernel: the velocity-Verlet substep (n_md + 1 launches per
     # step). Algorithmic bytes per atom and substep: ~100 (position hi + lo,

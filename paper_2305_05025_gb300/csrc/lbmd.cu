@@ -262,6 +262,11 @@ void fill_physics(lbmd_t h) {
     A.bwin = fine ? 5 : 3;
     for (int d = 0; d < 3; ++d) {
         A.bnc[d] = h->na == 0 ? 6 : fine ? (int)std::floor((double)Ls[d] / (0.5 * (rc + p.skin))) : A.nc[d];
+        // Folded axes: cells 128 apart share a bucket, and across the
+        // periodic wrap such cells are only (bnc mod 128) apart. Keep that
+        // at 0 or >= 7 (a few cells fewer, each slightly larger), so no
+        // search window of up to 7 consecutive cells meets a bucket twice.
+        if (A.bnc[d] > kFold && A.bnc[d] % kFold < kMaxWindow) A.bnc[d] -= A.bnc[d] % kFold;
         A.bfold[d] = A.bnc[d] < kFold ? A.bnc[d] : kFold;
         A.bfmask[d] = A.bnc[d] <= kFold ? -1 : kFold - 1;
         A.bh[d] = (float)((double)Ls[d] / A.bnc[d]);
@@ -690,6 +695,7 @@ lbmd_status lbmd_create(const lbmd_params *params, int n_atoms, const double *ma
             CREATE_TRY(dalloc_t(h, &A.sidx[g], (size_t)na));
         }
         CREATE_TRY(dalloc_t(h, &A.order, (size_t)na));
+        CREATE_TRY(dalloc_t(h, &A.scode, (size_t)na));
         CREATE_TRY(dalloc_t(h, &h->ident, (size_t)na));
         CREATE_TRY(dalloc_t(h, &A.nbr, (size_t)na * NL_MAX));
         CREATE_TRY(dalloc_t(h, &A.nnb, (size_t)na));

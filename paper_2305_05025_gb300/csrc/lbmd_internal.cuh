@@ -24,6 +24,7 @@ namespace lbmd {
 
 constexpr int kMortonBits = 7;                              // bucket coordinates < 128
 constexpr int kMortonCodes = 1 << (3 * kMortonBits);       // 2^21 Morton codes
+constexpr int kMaxWindow = 7;  // consecutive bucket cells along an axis that never meet a folded bucket twice (searches take 3 or 5)
 constexpr int NL_MAX = 256;    // neighbour-list capacity per atom (close packing of sigma = 0.4 beads within 1.3: ~200)
 
 struct AtomArgs {
@@ -61,6 +62,7 @@ struct AtomArgs {
     int *count[3], *slot[3], *bucket[3], *sidx[3];  // pair-search buckets by generation mod 3
     int fmask[3];         // bucket coordinate = cell & fmask (fold = nc, or 128 with mask 127)
     int *order;           // atoms in warp-sorted (Morton bucket) order
+    int *scode;           // per atom: Morton code of its 4x4x4 sub-cell within its bucket cell (sort key within a bucket)
     float4 *recP, *recL;  // adjoint recording ((n_md+1)*na): positions at x_k, or NULL
     float *recV, *recF;   // adjoint recording ((n_md+1)*3na): input velocity and force of kernel k
     int *nbr;             // na * NL_MAX neighbour lists (atom-major)

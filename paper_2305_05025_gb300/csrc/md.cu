@@ -322,6 +322,25 @@ __global__ void __launch_bounds__(1024) k_sort_top(AtomArgs A) {
     A.scan_block[2 * t + 1] = before + a0;
 }
 
+// Sub-cell of every atom within its bucket cell: 4 x 4 x 4 sub-cells in
+// Morton order (from the FP64 position), the sort key within a bucket.
+__global__ void __launch_bounds__(128) k_sort_code(AtomArgs A) {
+    const int a = blockIdx.x * blockDim.x + threadIdx.x;
+    if (a >= A.na) return;
+    unsigned code = 0;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        const double s = A.X[d * A.na + a] * ((double)A.bnc[d] / A.Ld[d]);
+        const double f = s - floor(s);
+        const unsigned c = f >= 0.0 && f < 1.0 ? min(3u, (unsigned)(f * 4.0)) : 0u;
+        code |= ((c & 1u) | ((c & 2u) << 2)) << d;
+    }
+    A.scode[a] = (int)code;
+}
+
+// Position of every atom in the sorted order: its bucket's offset plus its
+// rank within the bucket by (sub-cell code, slot), so the atoms a warp takes
+// from one bucket sit close together.
 __global__ void __launch_bounds__(128) k_sort_scatter(AtomArgs A) {
     const int a = blockIdx.x * blockDim.x + threadIdx.x;
     if (a >= A.na) return;
@@ -330,7 +349,18 @@ __global__ void __launch_bounds__(128) k_sort_scatter(AtomArgs A) {
     const int b = A.bucket[g3][a];
     const int x = b % A.bfold[0], y = (b / A.bfold[0]) % A.bfold[1], z = b / (A.bfold[0] * A.bfold[1]);
     const unsigned m = morton3(x, y, z);
-    const int pos = A.scan_block[m >> 10] + A.scan_local[m] + A.sidx[g3][a];
+    const int s = A.sidx[g3][a];
+    int rank = s;  // an atom past the bucket's capacity (an error already flagged) keeps its slot
+    if (s < A.bcap) {
+        const int n = min(A.count[g3][b], A.bcap);
+        const int mine = A.scode[a];
+        rank = 0;
+        for (int t = 0; t < n; ++t) {
+            const int c = A.scode[A.slot[g3][(size_t)b * A.bcap + t]];
+            rank += c < mine || (c == mine && t < s);
+        }
+    }
+    const int pos = A.scan_block[m >> 10] + A.scan_local[m] + rank;
     if (pos >= 0 && pos < A.na) A.order[pos] = a;
 }
 
@@ -563,19 +593,6 @@ __device__ __forceinline__ float4 shfl4(float4 v, int src) {
                        __shfl_sync(0xffffffffu, v.z, src), __shfl_sync(0xffffffffu, v.w, src));
 }
 
-// TPA lanes per atom, atoms in warp-sorted order (neighbouring warps touch
-// neighbouring atoms). Every load that depends only on the atom index is
-// issued at once, before any store, so a substep costs few dependent memory
-// latencies: the device step and flags, the atom index, the atom's state,
-// two per round of its list, and the bucket insertion. When the flag of this
-// generation is up the warp first rebuilds the lists of its atoms one after
-// the other (all 32 lanes on each); then each group evaluates its atom's
-// force over the list, lanes 0-2 of the group integrate one component each,
-// and lane 0 re-bins the atom.
-// Launch bounds: 8 lanes per atom at 9 blocks per SM (56 registers: the
-// 20k-atom grid fits one wave); 4 lanes at 10 blocks (48 registers): 8%
-// faster than 8 blocks at 64 registers on 200k atoms, where the grid takes
-// several waves and more resident warps hide more latency.
 // Component d of the velocity (sum f c + g/2)/rho of node (x, y, z) from the
 // populations pulled into it: the value the interpolation computes for its
 // nodes, with two running sums instead of the 19 pulled values.
@@ -609,6 +626,19 @@ __device__ __forceinline__ float far_velocity(const void *src, int store, const 
     return pulled_velocity<LBMD_BF16_SHIFTED>((const __nv_bfloat16 *)src, L, x, y, z, d);
 }
 
+// TPA lanes per atom, atoms in warp-sorted order (neighbouring warps touch
+// neighbouring atoms). Every load that depends only on the atom index is
+// issued at once, before any store, so a substep costs few dependent memory
+// latencies: the device step and flags, the atom index, the atom's state,
+// two per round of its list, and the bucket insertion. When the flag of this
+// generation is up the warp first rebuilds the lists of its atoms one after
+// the other (all 32 lanes on each); then each group evaluates its atom's
+// force over the list, lanes 0-2 of the group integrate one component each,
+// and lane 0 re-bins the atom.
+// Launch bounds: 8 lanes per atom at 9 blocks per SM (56 registers: the
+// 20k-atom grid fits one wave); 4 lanes at 10 blocks (48 registers): 8%
+// faster than 8 blocks at 64 registers on 200k atoms, where the grid takes
+// several waves and more resident warps hide more latency.
 template <int TPA, int NB, int W, bool RI>
 __global__ void __launch_bounds__(128, TPA == 8 ? 9 : 10) k_md_substep(AtomArgs A, int k) {
     const int lane = threadIdx.x & 31;
@@ -938,6 +968,7 @@ cudaError_t launch_md_sort(const AtomArgs &a, cudaStream_t s) {
     if (a.na == 0) return cudaSuccess;
     k_sort_local<<<kMortonCodes / 1024, 1024, 0, s>>>(a);
     k_sort_top<<<1, 1024, 0, s>>>(a);
+    k_sort_code<<<(a.na + 127) / 128, 128, 0, s>>>(a);
     k_sort_scatter<<<(a.na + 127) / 128, 128, 0, s>>>(a);
     return cudaGetLastError();
 }

@@ -93,7 +93,10 @@ def test_fast_atoms_beyond_the_frozen_region(orc, store):
     # 5e-3, most of it on nodes beyond the margin: far above the error.
     fg, _, _, _ = orc.run(dict(cfg, gamma=0.0), topo, f0, x0, v0, 1)
     assert np.abs(fo - fg).max() > 50 * ef
-    assert np.abs((pf1 + pa1) - (pf0 + pa0)).max() < 1e-5
+    # Momentum balance, up to the storage's rounding of the populations: the
+    # kicked nodes carry delta f ~ 0.02, whose FP16 step (scaled by 2^10) is
+    # ~1.5e-5 per population.
+    assert np.abs((pf1 + pa1) - (pf0 + pa0)).max() < (1e-5 if store == "f32" else 5e-4)
 
 
 @pytest.mark.parametrize("reinterp", [0, 1])
