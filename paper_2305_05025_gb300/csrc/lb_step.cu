@@ -118,22 +118,36 @@ __device__ __forceinline__ void pull_pair(const typename Store<S>::T *sp, ptrdif
                                           int ozp, bool wlo, bool whi, bool left_ok, bool right_ok, int xl, int xr,
                                           unsigned w[Q]) {
     using T = typename Store<S>::T;
+    // All 19 word loads first (and the edge lanes' 16-bit loads), so every
+    // load of the thread is in flight before the first shuffle waits on one.
+    const T *row[Q];
+    unsigned v[Q], edge[Q];
 #pragma unroll
     for (int i = 0; i < Q; ++i, sp += plane) {
         const int oyz = (cy(i) == 1 ? oym : (cy(i) == -1 ? oyp : 0)) + (cz(i) == 1 ? ozm : (cz(i) == -1 ? ozp : 0));
         const bool wall = W && ((cz(i) == 1 && wlo) || (cz(i) == -1 && whi));
-        const T *row = wall ? sp + (opp(i) - i) * plane : sp + oyz;
-        const unsigned v = __ldg(reinterpret_cast<const unsigned *>(row));
+        row[i] = wall ? sp + (opp(i) - i) * plane : sp + oyz;
+        v[i] = __ldg(reinterpret_cast<const unsigned *>(row[i]));
+    }
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        edge[i] = 0u;
+        if (cx(i) == 1 && !left_ok) edge[i] = (unsigned)__ldg(reinterpret_cast<const unsigned short *>(row[i] + xl)) << 16;
+        if (cx(i) == -1 && !right_ok) edge[i] = (unsigned)__ldg(reinterpret_cast<const unsigned short *>(row[i] + xr));
+    }
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        const bool wall = W && ((cz(i) == 1 && wlo) || (cz(i) == -1 && whi));
         if (cx(i) == 0) {
-            w[i] = v;
+            w[i] = v[i];
         } else if (cx(i) == 1) {  // x0 pulls x0 - 1 (high half of the left word), x0 + 1 pulls x0
-            unsigned prev = __shfl_up_sync(0xffffffffu, v, 1);
-            if (!left_ok) prev = (unsigned)__ldg(reinterpret_cast<const unsigned short *>(row + xl)) << 16;
-            w[i] = wall ? v : __byte_perm(prev, v, 0x5432);
+            unsigned prev = __shfl_up_sync(0xffffffffu, v[i], 1);
+            if (!left_ok) prev = edge[i];
+            w[i] = wall ? v[i] : __byte_perm(prev, v[i], 0x5432);
         } else {  // x0 pulls x0 + 1, x0 + 1 pulls x0 + 2 (low half of the right word)
-            unsigned next = __shfl_down_sync(0xffffffffu, v, 1);
-            if (!right_ok) next = (unsigned)__ldg(reinterpret_cast<const unsigned short *>(row + xr));
-            w[i] = wall ? v : __byte_perm(v, next, 0x5432);
+            unsigned next = __shfl_down_sync(0xffffffffu, v[i], 1);
+            if (!right_ok) next = edge[i];
+            w[i] = wall ? v[i] : __byte_perm(v[i], next, 0x5432);
         }
     }
 }
