@@ -18,6 +18,8 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "lbmd_internal.cuh"
 
 using namespace lbmd;
@@ -116,6 +118,16 @@ lbmd_status cuda_fail(lbmd_t h, cudaError_t e, const char *what) {
 
 // Device allocation with a test hook: LBMD_TEST_FAIL_ALLOC=k makes the k-th
 // allocation of a handle report failure (host-side fault injection).
+// NVTX range over one call of the ABI (header-only NVTX: free unless a
+// profiler is attached), so a timeline shows the calls around the graph
+// launches and kernels.
+struct Range {
+    explicit Range(const char *name) { nvtxRangePushA(name); }
+    ~Range() { nvtxRangePop(); }
+    Range(const Range &) = delete;
+    Range &operator=(const Range &) = delete;
+};
+
 lbmd_status dalloc(lbmd_t h, void **ptr, size_t bytes) {
     *ptr = nullptr;
     ++h->alloc_count;
@@ -773,6 +785,7 @@ void lbmd_destroy(lbmd_t h) {
 
 lbmd_status lbmd_set_state(lbmd_t h, const float *f, const float *rho, const float *u, const double *x,
                            const float *v, int on_device) {
+    const Range range("lbmd_set_state");
     if (!h) return fail(nullptr, LBMD_ERR_ARG, "handle is NULL");
     if (!f && (!rho || !u)) return fail(h, LBMD_ERR_ARG, "give f, or rho and u");
     if (h->na > 0 && (!x || !v)) return fail(h, LBMD_ERR_ARG, "x and v are required when n_atoms > 0");
@@ -827,6 +840,7 @@ lbmd_status lbmd_set_state(lbmd_t h, const float *f, const float *rho, const flo
 }
 
 lbmd_status lbmd_step(lbmd_t h, int n_steps) {
+    const Range range("lbmd_step");
     if (!h) return fail(nullptr, LBMD_ERR_ARG, "handle is NULL");
     if (n_steps < 0) return fail(h, LBMD_ERR_ARG, "n_steps must be >= 0");
     if (!h->state_set) return fail(h, LBMD_ERR_STATE, "lbmd_set_state has not been called");
@@ -840,6 +854,7 @@ lbmd_status lbmd_step(lbmd_t h, int n_steps) {
 }
 
 lbmd_status lbmd_get_fields(lbmd_t h, float *f, float *rho, float *u, double *x, float *v, int on_device) {
+    const Range range("lbmd_get_fields");
     if (!h) return fail(nullptr, LBMD_ERR_ARG, "handle is NULL");
     if (!h->state_set) return fail(h, LBMD_ERR_STATE, "lbmd_set_state has not been called");
     const Lat &L = h->L;
@@ -1050,6 +1065,7 @@ namespace {
 lbmd_status backward_impl(lbmd_t h, int n_steps, int ckpt_every, int observable, double *d_gamma, double *d_tau,
                           double *d_force_amp, double *obs, float *grad_f, float *grad_x, float *grad_v,
                           int on_device) {
+    const Range range("lbmd_backward");
     if (!h) return fail(nullptr, LBMD_ERR_ARG, "handle is NULL");
     if (!h->state_set) return fail(h, LBMD_ERR_STATE, "lbmd_set_state has not been called");
     if (n_steps < 1 || ckpt_every < 1) return fail(h, LBMD_ERR_ARG, "need n_steps >= 1 and ckpt_every >= 1");
