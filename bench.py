@@ -438,32 +438,37 @@ def run_ours(args, cfg):
     ms = prim["ms"]
     value = job_mlups(nodes, args.steps, world, ms * 1e-3)
 
-    # End to end through the public API with host buffers: every step copies
-    # the full state in (FP32 populations, positions, velocities) from pinned
-    # host memory, advances one step and copies the state out again.
+    # End to end through the public API with host buffers: every step loads
+    # the whole state (the populations in their storage format, positions,
+    # velocities) from pinned host memory with lbmd_load_state, advances one
+    # step and saves the state back with lbmd_save_state.
     h = handle
-    e2e_steps = 0 if args.no_e2e else 3
-    pin = {"f": torch.empty((19, nodes), dtype=torch.float32, pin_memory=True),
-           "x": torch.empty((3, na), dtype=torch.float64, pin_memory=True),
-           "v": torch.empty((3, na), dtype=torch.float32, pin_memory=True)}
-    outs = {k: torch.empty_like(t).pin_memory() for k, t in pin.items()}
-    import ctypes as C
+    e2e_steps = 0 if args.no_e2e else 5
+    io_bytes = 0
+    e2e_s = 0.0
+    if e2e_steps:
+        import ctypes as C
 
-    L = lbmd.lib()
-    vp = lambda t: C.c_void_p(t.data_ptr())
-    assert L.lbmd_get_fields(h, vp(pin["f"]), None, None, vp(pin["x"]), vp(pin["v"]), 0) == 0
-    barrier()
-    e0 = time.perf_counter()
-    for _ in range(e2e_steps):
-        assert L.lbmd_set_state(h, vp(pin["f"]), None, None, vp(pin["x"]), vp(pin["v"]), 0) == 0
-        assert L.lbmd_step(h, 1) == 0
-        assert L.lbmd_get_fields(h, vp(outs["f"]), None, None, vp(outs["x"]), vp(outs["v"]), 0) == 0
-    barrier()
-    e2e_s = (time.perf_counter() - e0) / max(e2e_steps, 1)
-    e2e_s, = reduce_max([e2e_s])
-    io_bytes = sum(t.numel() * t.element_size() for t in pin.values())
+        pop_t = torch.float32 if stores[0] == "f32" else torch.int16
+        pin = {"pop": torch.empty((19, nodes), dtype=pop_t, pin_memory=True),
+               "x": torch.empty((3, na), dtype=torch.float64, pin_memory=True),
+               "v": torch.empty((3, na), dtype=torch.float32, pin_memory=True)}
+        outs = {k: torch.empty_like(t).pin_memory() for k, t in pin.items()}
+        L = lbmd.lib()
+        vp = lambda t: C.c_void_p(t.data_ptr()) if t.numel() else None
+        assert L.lbmd_save_state(h, vp(pin["pop"]), vp(pin["x"]), vp(pin["v"]), 0) == 0
+        barrier()
+        e0 = time.perf_counter()
+        for _ in range(e2e_steps):
+            assert L.lbmd_load_state(h, vp(pin["pop"]), vp(pin["x"]), vp(pin["v"]), 0) == 0
+            assert L.lbmd_step(h, 1) == 0
+            assert L.lbmd_save_state(h, vp(outs["pop"]), vp(outs["x"]), vp(outs["v"]), 0) == 0
+        barrier()
+        e2e_s = (time.perf_counter() - e0) / e2e_steps
+        e2e_s, = reduce_max([e2e_s])
+        io_bytes = sum(t.numel() * t.element_size() for t in pin.values())
+        del pin, outs
     lbmd.lbmd_destroy(h)
-    del pin, outs
 
     launches = (n_md + 9) if na > 0 else 2  # 4 sort + interp + (n_md + 1) substeps + spread + dense + fix-up
     lat_roof = {s: _lattice_roofline(s, nodes, runs[s]["lb_ms"], hbm, peak_kind) for s in stores}

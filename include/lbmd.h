@@ -135,6 +135,24 @@ lbmd_status lbmd_set_state(lbmd_t h, const float *f, const float *rho, const flo
  * only when check_every > 0 and a multiple of it is crossed. */
 lbmd_status lbmd_step(lbmd_t h, int n_steps);
 
+/* Snapshot of the state in the storage format (no counterpart in the paper:
+ * checkpoint and restore, and the cheapest exchange with the host). pop
+ * receives the lattice buffer the next step reads: 19*N elements of the
+ * storage format (4 bytes for LBMD_F32, 2 for the 16-bit formats, which hold
+ * delta f = f - w_i rho0, FP16 scaled by 2^10) in the library's
+ * post-collision layout; treat it as opaque and give it back to
+ * lbmd_load_state on a handle created with the same lattice size and
+ * storage format. x (3*n_atoms FP64) and v (3*n_atoms FP32) as
+ * lbmd_get_fields. Any pointer may be NULL; on_device: 1 if they are device
+ * memory. Synchronises the stream when on_device = 0. */
+lbmd_status lbmd_save_state(lbmd_t h, void *pop, double *x, float *v, int on_device);
+
+/* Restores a snapshot of lbmd_save_state: the lattice bit for bit; the atoms
+ * as lbmd_set_state sets them (forces and pair-search cells recomputed). The
+ * step counter restarts at 0 (the thermal noise draws restart with it). pop
+ * is required, x and v when n_atoms > 0 (LBMD_ERR_ARG otherwise). */
+lbmd_status lbmd_load_state(lbmd_t h, const void *pop, const double *x, const float *v, int on_device);
+
 /* Copies out the current state (Sec. 2.2; rho and u are the moments of
  * Eq. 2); any pointer may be NULL. f: FP32 post-streaming populations (19*N); rho (N); u (3*N), the velocity
  * (sum f c + g/2)/rho; x (3*n_atoms FP64); v (3*n_atoms FP32). Synchronises

@@ -600,6 +600,11 @@ lbmd_status ana_alloc(lbmd_t h, void **p, size_t bytes) {
     return LBMD_OK;
 }
 
+// Bytes of one population buffer in the handle's storage format.
+size_t pop_bytes(lbmd_t h) { return h->L.N * Q * store_bytes(h->p.store); }
+
+lbmd_status finish_state(lbmd_t h, const double *x, const float *v, int on_device);
+
 }  // namespace
 
 extern "C" {
@@ -805,6 +810,42 @@ lbmd_status lbmd_set_state(lbmd_t h, const float *f, const float *rho, const flo
         }
     }
     CK(h, launch_lb_init(h->p.store, L, h->pop[0], f ? df : nullptr, f ? nullptr : drho, f ? nullptr : du, h->stream));
+    return finish_state(h, x, v, on_device);
+}
+
+lbmd_status lbmd_save_state(lbmd_t h, void *pop, double *x, float *v, int on_device) {
+    const Range range("lbmd_save_state");
+    if (!h) return fail(nullptr, LBMD_ERR_ARG, "handle is NULL");
+    if (!h->state_set) return fail(h, LBMD_ERR_STATE, "lbmd_set_state has not been called");
+    const cudaMemcpyKind k = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    if (pop) CK(h, cudaMemcpyAsync(pop, h->pop[h->steps & 1], pop_bytes(h), k, h->stream));
+    if (h->na > 0) {
+        if (x) CK(h, cudaMemcpyAsync(x, h->A.X, 3 * (size_t)h->na * sizeof(double), k, h->stream));
+        if (v) CK(h, cudaMemcpyAsync(v, h->A.V, 3 * (size_t)h->na * sizeof(float), k, h->stream));
+    }
+    if (!on_device) CK(h, cudaStreamSynchronize(h->stream));
+    return LBMD_OK;
+}
+
+lbmd_status lbmd_load_state(lbmd_t h, const void *pop, const double *x, const float *v, int on_device) {
+    const Range range("lbmd_load_state");
+    if (!h) return fail(nullptr, LBMD_ERR_ARG, "handle is NULL");
+    if (!pop) return fail(h, LBMD_ERR_ARG, "pop is NULL");
+    if (h->na > 0 && (!x || !v)) return fail(h, LBMD_ERR_ARG, "x and v are required when n_atoms > 0");
+    TRY(to_device(h, h->pop[0], pop, pop_bytes(h), on_device));
+    return finish_state(h, x, v, on_device);
+}
+
+}  // extern "C"
+
+namespace {
+
+// The part of setting a state shared by lbmd_set_state and lbmd_load_state,
+// once the populations are in buffer 0: device state, touched tags and
+// coupling force cleared, atoms uploaded with their first forces and cells,
+// the lattice scanned for non-finite values.
+lbmd_status finish_state(lbmd_t h, const double *x, const float *v, int on_device) {
+    const Lat &L = h->L;
     CK(h, cudaMemsetAsync(h->ds, 0, sizeof(DevState), h->stream));
     CK(h, cudaMemsetAsync(h->C.tag, 0, L.N * sizeof(int), h->stream));
     CK(h, cudaMemsetAsync(h->C.G, 0, L.N * sizeof(float4), h->stream));
@@ -838,6 +879,10 @@ lbmd_status lbmd_set_state(lbmd_t h, const float *f, const float *rho, const flo
     h->steps = 0;
     return read_flags(h);
 }
+
+}  // namespace
+
+extern "C" {
 
 lbmd_status lbmd_step(lbmd_t h, int n_steps) {
     const Range range("lbmd_step");

@@ -73,6 +73,8 @@ def lib():
         L.lbmd_set_state.argtypes = [vp, vp, vp, vp, vp, vp, ip]
         L.lbmd_step.argtypes = [vp, ip]
         L.lbmd_get_fields.argtypes = [vp, vp, vp, vp, vp, vp, ip]
+        L.lbmd_save_state.argtypes = [vp, vp, vp, vp, ip]
+        L.lbmd_load_state.argtypes = [vp, vp, vp, vp, ip]
         L.lbmd_get_stats.argtypes = [vp, dp, dp, dp]
         L.lbmd_check.argtypes = [vp]
         L.lbmd_cell_list.argtypes = [vp, vp, vp, vp, ip]
@@ -234,6 +236,56 @@ def lbmd_get_fields(h, f=False, rho=False, u=False, x=False, v=False, out=None):
     p = lambda k: res[k].ctypes.data_as(C.c_void_p) if k in res else None
     _check(h, lib().lbmd_get_fields(h, p("f"), p("rho"), p("u"), p("x"), p("v"), 0))
     return res
+
+
+def _pop_dtype(h):
+    """Element type of the handle's population storage (the raw snapshot)."""
+    return np.float32 if h.params.store == STORES["f32"] else np.uint16
+
+
+def lbmd_save_state(h, out=None):
+    """Raw snapshot (pop in the storage format, x, v) as numpy arrays; with
+    `out` (a dict of CUDA tensors "pop" (float32 or int16/uint16-sized), "x",
+    "v") fills those on the device."""
+    N, na = h.N, h.n_atoms
+    if out is not None:
+        keep = []
+        pop = out["pop"]
+        if not (_is_torch(pop) and pop.is_cuda and pop.is_contiguous()
+                and pop.numel() * pop.element_size() == Q * N * np.dtype(_pop_dtype(h)).itemsize):
+            raise ValueError("pop: a contiguous CUDA tensor of 19*N storage elements")
+        px, _ = _ptr(out.get("x"), np.float64, (3, na), keep)
+        pv, _ = _ptr(out.get("v"), np.float32, (3, na), keep)
+        _check(h, lib().lbmd_save_state(h, C.c_void_p(pop.data_ptr()), px, pv, 1))
+        return out
+    res = {"pop": np.zeros((Q, N), _pop_dtype(h)), "x": np.zeros((3, na), np.float64), "v": np.zeros((3, na), np.float32)}
+    p = lambda k: res[k].ctypes.data_as(C.c_void_p)
+    _check(h, lib().lbmd_save_state(h, p("pop"), p("x") if na else None, p("v") if na else None, 0))
+    return res
+
+
+def lbmd_load_state(h, pop, x=None, v=None):
+    """Restores a snapshot of lbmd_save_state (numpy arrays, or CUDA tensors
+    for all three)."""
+    N, na = h.N, h.n_atoms
+    keep = []
+    if _is_torch(pop):
+        if not (pop.is_cuda and pop.is_contiguous()
+                and pop.numel() * pop.element_size() == Q * N * np.dtype(_pop_dtype(h)).itemsize):
+            raise ValueError("pop: a contiguous CUDA tensor of 19*N storage elements")
+        pp, dp_ = C.c_void_p(pop.data_ptr()), 1
+        keep.append(pop)
+    else:
+        arr = np.ascontiguousarray(np.asarray(pop, dtype=_pop_dtype(h)))
+        if arr.size != Q * N:
+            raise ValueError(f"expected {Q * N} elements, got {arr.size}")
+        keep.append(arr)
+        pp, dp_ = arr.ctypes.data_as(C.c_void_p), 0
+    px, d1 = _ptr(x, np.float64, (3, na), keep)
+    pv, d2 = _ptr(v, np.float32, (3, na), keep)
+    if any(d is not None and d != dp_ for d in (d1, d2)):
+        raise ValueError("mix of host and device inputs")
+    _check(h, lib().lbmd_load_state(h, pp, px, pv, dp_))
 
 
 def lbmd_get_stats(h):
