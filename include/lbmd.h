@@ -233,7 +233,10 @@ lbmd_status lbmd_set_thermal(lbmd_t h, double kT, uint64_t seed);
  * lattice kernel of the NEXT step launch to two
  * caller events (cudaEvent_t, created with timing enabled), so the caller can
  * time that kernel with cudaEventElapsedTime on the stream it runs on.
- * NULL, NULL restores the library's own events. */
+ * NULL, NULL restores the library's own events. The events stay referenced
+ * by the step graph until the next call replaces them: the caller keeps them
+ * alive until then (destroying them first makes the next call fail with
+ * LBMD_ERR_CUDA). */
 lbmd_status lbmd_set_timing_events(lbmd_t h, void *ev_start, void *ev_stop);
 
 /* Timing hook (no counterpart in the paper). Like lbmd_set_timing_events,
