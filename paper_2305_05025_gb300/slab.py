@@ -132,3 +132,89 @@ def torch_empty_like(t):
     import torch
 
     return torch.empty_like(t)
+
+
+def _exchange_rows(send_lo, send_hi, rank, world, group=None, tag=0):
+    """Sends the float64 row block send_lo (k, m_lo) to the lower neighbour
+    and send_hi (k, m_hi) to the upper one; returns the blocks received from
+    the lower and the upper neighbour. Counts go first, so the blocks may
+    have any length (0 included)."""
+    import torch
+    import torch.distributed as dist
+
+    lo, hi = neighbours(rank, world)
+    k = send_lo.shape[0]
+    n_out = [torch.tensor([send_lo.shape[1]], dtype=torch.int64), torch.tensor([send_hi.shape[1]], dtype=torch.int64)]
+    n_in = [torch.zeros(1, dtype=torch.int64), torch.zeros(1, dtype=torch.int64)]
+    ops = [dist.P2POp(dist.isend, n_out[0], lo, group, tag + 1), dist.P2POp(dist.irecv, n_in[1], hi, group, tag + 1),
+           dist.P2POp(dist.isend, n_out[1], hi, group, tag + 2), dist.P2POp(dist.irecv, n_in[0], lo, group, tag + 2)]
+    for r in dist.batch_isend_irecv(ops):
+        r.wait()
+    r_lo = torch.zeros((k, int(n_in[0])), dtype=torch.float64)
+    r_hi = torch.zeros((k, int(n_in[1])), dtype=torch.float64)
+    ops = []
+    if send_lo.shape[1]:
+        ops.append(dist.P2POp(dist.isend, send_lo.contiguous(), lo, group, tag + 3))
+    if r_hi.shape[1]:
+        ops.append(dist.P2POp(dist.irecv, r_hi, hi, group, tag + 3))
+    if send_hi.shape[1]:
+        ops.append(dist.P2POp(dist.isend, send_hi.contiguous(), hi, group, tag + 4))
+    if r_lo.shape[1]:
+        ops.append(dist.P2POp(dist.irecv, r_lo, lo, group, tag + 4))
+    if ops:
+        for r in dist.batch_isend_irecv(ops):
+            r.wait()
+    return r_lo, r_hi
+
+
+def migrate_atoms(ids, x, v, rank, ranges, nz, group=None):
+    """Once per step: the atoms a rank holds whose position left its slab go
+    to the neighbour that now owns them (an atom moves far less than a slab
+    per step, so only the two neighbours can be the new owner). ids (n,)
+    global atom indices, x (3, n) unwrapped FP64 positions, v (3, n); returns
+    the rank's atoms after the exchange, in the same layout, sorted by id."""
+    import torch
+
+    world = len(ranges)
+    if world == 1:
+        order = np.argsort(ids, kind="stable")
+        return ids[order], x[:, order], v[:, order]
+    lo, hi = neighbours(rank, world)
+    owner = atom_owner(x[2], ranges, nz)
+    stay = owner == rank
+    if not np.all(stay | (owner == lo) | (owner == hi)):
+        raise ValueError("an atom moved past a neighbouring slab in one step")
+    pack = lambda m: torch.from_numpy(np.vstack([ids[m][None].astype(np.float64), x[:, m], v[:, m]]))
+    # With two ranks both neighbours are the same rank: send everything leaving once.
+    to_lo = (owner == lo) & ~stay
+    to_hi = (owner == hi) & ~stay & ~to_lo
+    r_lo, r_hi = _exchange_rows(pack(to_lo), pack(to_hi), rank, world, group, tag=10)
+    got = np.hstack([np.vstack([ids[stay][None].astype(np.float64), x[:, stay], v[:, stay]]), r_lo.numpy(), r_hi.numpy()])
+    order = np.argsort(got[0], kind="stable")
+    got = got[:, order]
+    return got[0].astype(np.int64), got[1:4], got[4:7]
+
+
+def exchange_ghosts(ids, x, rank, ranges, nz, width, group=None):
+    """Every substep: the positions of this rank's atoms within `width` (the
+    pair-list radius) of its lower and upper faces go to the neighbour on that
+    side; returns (ghost ids, ghost positions) received, the other ranks'
+    atoms within `width` of this slab (those ghost_atoms names). Slabs are
+    assumed thicker than `width`, so only the neighbours hold ghosts."""
+    import torch
+
+    world = len(ranges)
+    if world == 1:
+        return np.zeros(0, np.int64), np.zeros((3, 0))
+    lo, hi = neighbours(rank, world)
+    z0, z1 = ranges[rank]
+    zw = np.asarray(x[2], np.float64) % nz
+    near_lo = (zw - z0) % nz <= width  # within width above the lower face
+    near_hi = (z1 - zw) % nz <= width  # within width below the upper face
+    pack = lambda m: torch.from_numpy(np.vstack([ids[m][None].astype(np.float64), x[:, m]]))
+    if world == 2:  # one neighbour on both sides: send the union once
+        r_lo, r_hi = _exchange_rows(pack(near_lo | near_hi), pack(np.zeros_like(near_lo)), rank, world, group, tag=20)
+    else:
+        r_lo, r_hi = _exchange_rows(pack(near_lo), pack(near_hi), rank, world, group, tag=20)
+    got = np.hstack([r_lo.numpy(), r_hi.numpy()])
+    return got[0].astype(np.int64), got[1:4]

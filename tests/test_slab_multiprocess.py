@@ -154,3 +154,71 @@ def test_ownership_and_ghosts():
             if dist_ <= width:
                 expect.add(i)
         assert gh == expect, r
+
+
+def _migrate_rank(rank, world, port, q):
+    import sys
+
+    sys.path.insert(0, ROOT)
+    from paper_2305_05025_gb300 import slab
+
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    nz, n, width = 24, 3000, 1.1
+    rng = np.random.default_rng(11)
+    x_all = rng.uniform(-30, 30, (3, n))
+    v_all = rng.standard_normal((3, n))
+    ranges = slab.slab_ranges(nz, world)
+    mine = slab.atom_owner(x_all[2], ranges, nz) == rank
+    ids = np.nonzero(mine)[0]
+    # One step of motion: every atom moves by less than one plane.
+    step = rng.uniform(-0.9, 0.9, (3, n))
+    x_new = x_all + step
+    got_ids, got_x, got_v = slab.migrate_atoms(ids, x_new[:, ids], v_all[:, ids], rank, ranges, nz)
+    gh_ids, gh_x = slab.exchange_ghosts(got_ids, got_x, rank, ranges, nz, width)
+    q.put((rank, got_ids, got_x, got_v, gh_ids, gh_x))
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+@pytest.mark.parametrize("world", [2, 3])
+def test_atom_migration_and_ghost_exchange(world):
+    """After one step of motion each rank holds exactly the atoms its slab
+    owns (none lost, none twice, positions and velocities carried), and the
+    ghost positions it receives are the other ranks' atoms within the list
+    radius of its slab (brute force over all atoms)."""
+    import sys
+
+    sys.path.insert(0, ROOT)
+    from paper_2305_05025_gb300 import slab
+
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_migrate_rank, args=(r, world, port, q)) for r in range(world)]
+    for p in procs:
+        p.start()
+    res = {}
+    for _ in range(world):
+        r, *rest = q.get(timeout=300)
+        res[r] = rest
+    for p in procs:
+        p.join(timeout=120)
+        assert p.exitcode == 0
+    nz, n, width = 24, 3000, 1.1
+    rng = np.random.default_rng(11)
+    x_all = rng.uniform(-30, 30, (3, n))
+    v_all = rng.standard_normal((3, n))
+    x_new = x_all + rng.uniform(-0.9, 0.9, (3, n))
+    ranges = slab.slab_ranges(nz, world)
+    owner = slab.atom_owner(x_new[2], ranges, nz)
+    seen = np.concatenate([res[r][0] for r in range(world)])
+    assert np.array_equal(np.sort(seen), np.arange(n))
+    for r in range(world):
+        ids, xr, vr, gh_ids, gh_x = res[r]
+        assert np.array_equal(ids, np.nonzero(owner == r)[0])
+        assert np.array_equal(xr, x_new[:, ids]) and np.array_equal(vr, v_all[:, ids])
+        expect = slab.ghost_atoms(x_new[2], r, ranges, nz, width)
+        assert np.array_equal(np.sort(gh_ids), np.sort(expect)), r
+        order = np.argsort(gh_ids)
+        assert np.array_equal(gh_x[:, order], x_new[:, np.sort(gh_ids)])
