@@ -750,10 +750,10 @@ __global__ void __launch_bounds__(128, TPA == 8 ? 9 : 10) k_md_substep(AtomArgs 
             const int xx = o[0] ? (bcell[0] + 1 == A.nl[0] ? 0 : bcell[0] + 1) : bcell[0];
             const int yy = o[1] ? (bcell[1] + 1 == A.nl[1] ? 0 : bcell[1] + 1) : bcell[1];
             const int zz = o[2] ? (bcell[2] + 1 == A.nl[2] ? 0 : bcell[2] + 1) : bcell[2];
-            const float W = (o[0] ? wt[0] : 1.f - wt[0]) * (o[1] ? wt[1] : 1.f - wt[1]) * (o[2] ? wt[2] : 1.f - wt[2]);
+            const float Wt = (o[0] ? wt[0] : 1.f - wt[0]) * (o[1] ? wt[1] : 1.f - wt[1]) * (o[2] ? wt[2] : 1.f - wt[2]);
             const float4 un = A.unode[((size_t)zz * A.nl[1] + yy) * A.nl[0] + xx];
             if (__float_as_int(un.w) == stamp)
-                u += W * (sub == 0 ? un.x : (sub == 1 ? un.y : un.z));
+                u += Wt * (sub == 0 ? un.x : (sub == 1 ? un.y : un.z));
             else
                 far |= 1u << j;
         }
@@ -771,8 +771,8 @@ __global__ void __launch_bounds__(128, TPA == 8 ? 9 : 10) k_md_substep(AtomArgs 
             const int xx = o[0] ? (bcell[0] + 1 == A.nl[0] ? 0 : bcell[0] + 1) : bcell[0];
             const int yy = o[1] ? (bcell[1] + 1 == A.nl[1] ? 0 : bcell[1] + 1) : bcell[1];
             const int zz = o[2] ? (bcell[2] + 1 == A.nl[2] ? 0 : bcell[2] + 1) : bcell[2];
-            const float W = (o[0] ? wt[0] : 1.f - wt[0]) * (o[1] ? wt[1] : 1.f - wt[1]) * (o[2] ? wt[2] : 1.f - wt[2]);
-            u += W * far_velocity(A.pop[step & 1], A.store, A.lat, xx, yy, zz, sub);
+            const float Wt = (o[0] ? wt[0] : 1.f - wt[0]) * (o[1] ? wt[1] : 1.f - wt[1]) * (o[2] ? wt[2] : 1.f - wt[2]);
+            u += Wt * far_velocity(A.pop[step & 1], A.store, A.lat, xx, yy, zz, sub);
             const int node = (int)(((size_t)zz * A.nl[1] + yy) * A.nl[0] + xx);
             if (sub == 0 && A.tag[node] != stamp && atomicExch(&A.tag[node], stamp) != stamp) {
                 const int t = atomicAdd(&A.ds->n_touched, 1);
@@ -839,9 +839,9 @@ __global__ void __launch_bounds__(128, TPA == 8 ? 9 : 10) k_md_substep(AtomArgs 
                 const int xx = o[0] ? (bcell[0] + 1 == A.nl[0] ? 0 : bcell[0] + 1) : bcell[0];
                 const int yy = o[1] ? (bcell[1] + 1 == A.nl[1] ? 0 : bcell[1] + 1) : bcell[1];
                 const int zz = o[2] ? (bcell[2] + 1 == A.nl[2] ? 0 : bcell[2] + 1) : bcell[2];
-                const float W =
+                const float Wt =
                     (o[0] ? wt[0] : 1.f - wt[0]) * (o[1] ? wt[1] : 1.f - wt[1]) * (o[2] ? wt[2] : 1.f - wt[2]);
-                atomicAdd(&A.G[((size_t)zz * A.nl[1] + yy) * A.nl[0] + xx], make_float4(-W * jx, -W * jy, -W * jz, 0.f));
+                atomicAdd(&A.G[((size_t)zz * A.nl[1] + yy) * A.nl[0] + xx], make_float4(-Wt * jx, -Wt * jy, -Wt * jz, 0.f));
             }
         }
     }
