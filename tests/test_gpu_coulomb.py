@@ -1,7 +1,7 @@
 """GPU screened Coulomb pairs (the force field's electrostatics with a
 distance-dependent dielectric and a cutoff, Sec. 2.2) against the FP64
 oracle: a charged 500-bead chain, teacher-forced over ten coupled steps
-(bound max(1e-5, 2 x the FP32 floor) per field, as the other coupled tests),
+(bound max(1e-5, 3 x the FP32 floor) per field, as the other coupled tests),
 the adjoint of a short charged Lennard-Jones chain against the oracle's
 converged central differences, and the setter's argument errors."""
 import numpy as np
