@@ -97,7 +97,11 @@ typedef struct {
     int force_wave_axis;      /* axis of the Kolmogorov wave (0, 1, 2) */
     int walls_z;              /* 1: half-way bounce-back walls at z = -1/2, nz - 1/2 */
     int store;                /* LBMD_F32, LBMD_F16_SHIFTED, LBMD_BF16_SHIFTED */
-    int deterministic;        /* reserved, must be 0 */
+    int deterministic;        /* 1: bitwise-reproducible lbmd_step (Verlet lists sorted by
+                                 atom index, the spread summed in exact fixed point,
+                                 set-up forces in fixed point); 0: the default, faster
+                                 order-of-atomics sums. Mode 1 refuses the
+                                 re-interpolated coupling and lbmd_backward. */
     int check_every;          /* lbmd_step polls the device error flags every this
                                  many steps (0: only lbmd_check / lbmd_get_stats do) */
 } lbmd_params;

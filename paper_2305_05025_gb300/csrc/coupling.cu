@@ -145,10 +145,12 @@ __global__ void __launch_bounds__(128) k_interp(CouplingArgs C, AtomArgs A, cons
             const int node = (int)(((size_t)zz * L.ny + yy) * L.nx + xx);
             if (C.tag[node] != stamp && atomicExch(&C.tag[node], stamp) != stamp) {
                 const int j = atomicAdd(&C.ds->n_touched, 1);
-                if (j < C.touched_cap)
+                if (j < C.touched_cap) {
                     C.touched[j] = node;
-                else
+                    if (C.tslot) C.tslot[node] = j;
+                } else {
                     atomicOr(&C.ds->flags, FLAG_TOUCHED);
+                }
             }
         }
     } else if (valid && C.reinterp) {
@@ -173,10 +175,12 @@ __global__ void __launch_bounds__(128) k_interp(CouplingArgs C, AtomArgs A, cons
             }
             if (C.tag[node] != stamp && atomicExch(&C.tag[node], stamp) != stamp) {
                 const int j = atomicAdd(&C.ds->n_touched, 1);
-                if (j < C.touched_cap)
+                if (j < C.touched_cap) {
                     C.touched[j] = node;
-                else
+                    if (C.tslot) C.tslot[node] = j;
+                } else {
                     atomicOr(&C.ds->flags, FLAG_TOUCHED);
+                }
             }
         }
     } else if (valid) {
@@ -197,10 +201,12 @@ __global__ void __launch_bounds__(128) k_interp(CouplingArgs C, AtomArgs A, cons
             const int node = (int)(((size_t)nzk * L.ny + nyk) * L.nx + nxk);
             if (C.tag[node] != stamp && atomicExch(&C.tag[node], stamp) != stamp) {
                 const int j = atomicAdd(&C.ds->n_touched, 1);
-                if (j < C.touched_cap)
+                if (j < C.touched_cap) {
                     C.touched[j] = node;
-                else
+                    if (C.tslot) C.tslot[node] = j;
+                } else {
                     atomicOr(&C.ds->flags, FLAG_TOUCHED);
+                }
             }
         }
     }
@@ -236,7 +242,15 @@ __global__ void __launch_bounds__(128) k_spread(CouplingArgs C) {
         const int nzk = o[2] ? (b[2] + 1 == L.nz ? 0 : b[2] + 1) : b[2];
         const float W = (o[0] ? t[0] : 1.f - t[0]) * (o[1] ? t[1] : 1.f - t[1]) * (o[2] ? t[2] : 1.f - t[2]);
         const size_t node = ((size_t)nzk * L.ny + nyk) * L.nx + nxk;
-        atomicAdd(&C.G[node], make_float4(-W * J[0], -W * J[1], -W * J[2], 0.f));
+        if (C.gfix) {  // deterministic: exact integer sums in the node's touched slot
+            long long *g = C.gfix + 3 * (size_t)C.tslot[node];
+#pragma unroll
+            for (int d = 0; d < 3; ++d)
+                atomicAdd(reinterpret_cast<unsigned long long *>(g + d),
+                          (unsigned long long)llrint((double)(-W * J[d]) * kFixScale));
+        } else {
+            atomicAdd(&C.G[node], make_float4(-W * J[0], -W * J[1], -W * J[2], 0.f));
+        }
     }
 }
 

@@ -14,7 +14,8 @@ namespace {
 // last block to finish advances the step counter and empties the list.
 template <int S>
 __global__ void __launch_bounds__(256) k_lb_fix(Lat L, typename Store<S>::T *b0, typename Store<S>::T *b1,
-                                                const int *touched, int cap, float4 *G, DevState *ds, int keep) {
+                                                const int *touched, int cap, float4 *G, long long *gfix, DevState *ds,
+                                                int keep) {
     const int cnt = min(ds->n_touched, cap);
     const int step = ds->step;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < cnt; i += gridDim.x * blockDim.x) {
@@ -27,7 +28,15 @@ __global__ void __launch_bounds__(256) k_lb_fix(Lat L, typename Store<S>::T *b0,
         float f[Q], F[3];
         pull<S>(src, L, x, y, z, f);
         body_force(L, x, y, z, F);
-        const float4 Gn = G[node];
+        float4 Gn;
+        if (gfix) {  // deterministic mode: the exact fixed-point sums of this touched slot
+            long long *g = gfix + 3 * (size_t)i;
+            Gn = make_float4((float)((double)g[0] / kFixScale), (float)((double)g[1] / kFixScale),
+                             (float)((double)g[2] / kFixScale), 0.f);
+            g[0] = g[1] = g[2] = 0;
+        } else {
+            Gn = G[node];
+        }
         F[0] += Gn.x;
         F[1] += Gn.y;
         F[2] += Gn.z;
@@ -224,7 +233,7 @@ __global__ void k_reduce_finish(const double *partials, int nblocks, int width, 
 cudaError_t launch_lb_fix(int store, const Lat &L, void *const buf[2], const CouplingArgs &c, int grid,
                           cudaStream_t s) {
     LBMD_DISPATCH(store, (k_lb_fix<SV><<<grid, 256, 0, s>>>(L, (T *)buf[0], (T *)buf[1], c.touched, c.touched_cap,
-                                                             c.G, c.ds, c.keep)));
+                                                             c.G, c.gfix, c.ds, c.keep)));
     return cudaGetLastError();
 }
 

@@ -174,7 +174,7 @@ std::string validate(const lbmd_params *p, int n_atoms, const double *mass, int 
     if (!std::isfinite(p->force_amp)) return "force_amp must be finite";
     if (p->walls_z != 0 && p->walls_z != 1) return "walls_z must be 0 or 1";
     if (p->walls_z && p->nz < 2) return "walls_z needs nz >= 2";
-    if (p->deterministic != 0) return "deterministic mode is not available";
+    if (p->deterministic != 0 && p->deterministic != 1) return "deterministic must be 0 or 1";
     if (p->check_every < 0) return "check_every must be >= 0";
     if (n_atoms < 0) return "n_atoms must be >= 0";
     if (n_bonds < 0) return "n_bonds must be >= 0";
@@ -249,6 +249,7 @@ void fill_physics(lbmd_t h) {
     A.rc2f = (float)(rc * rc);
     A.rl2 = (float)((rc + p.skin) * (rc + p.skin));
     A.half_skin2 = (float)(0.25 * p.skin * p.skin);
+    A.det = p.deterministic;
     A.rc2d = rc * rc;
     const int Ls[3] = {p.nx, p.ny, p.nz};
     for (int d = 0; d < 3; ++d) {
@@ -704,6 +705,12 @@ lbmd_status lbmd_create(const lbmd_params *params, int n_atoms, const double *ma
         CREATE_TRY(dalloc_t(h, &C.frac, na3));
         C.touched_cap = 8 * na;
         CREATE_TRY(dalloc_t(h, &C.touched, (size_t)C.touched_cap));
+        if (h->p.deterministic) {  // node -> touched slot, and the fixed-point sums per slot
+            CREATE_TRY(dalloc_t(h, &C.tslot, L.N));
+            CREATE_TRY(dalloc_t(h, &C.gfix, 3 * (size_t)C.touched_cap));
+            CREATE_CK(cudaMemsetAsync(C.tslot, 0, L.N * sizeof(int), h->stream));
+            CREATE_CK(cudaMemsetAsync(C.gfix, 0, 3 * (size_t)C.touched_cap * sizeof(long long), h->stream));
+        }
         const size_t B = (size_t)A.bfold[0] * A.bfold[1] * A.bfold[2];
         for (int g = 0; g < 3; ++g) {
             CREATE_TRY(dalloc_t(h, &A.count[g], B));
@@ -849,6 +856,8 @@ lbmd_status finish_state(lbmd_t h, const double *x, const float *v, int on_devic
     CK(h, cudaMemsetAsync(h->ds, 0, sizeof(DevState), h->stream));
     CK(h, cudaMemsetAsync(h->C.tag, 0, L.N * sizeof(int), h->stream));
     CK(h, cudaMemsetAsync(h->C.G, 0, L.N * sizeof(float4), h->stream));
+    if (h->C.gfix)
+        CK(h, cudaMemsetAsync(h->C.gfix, 0, 3 * (size_t)h->C.touched_cap * sizeof(long long), h->stream));
     if (h->na > 0) {
         const size_t na3 = (size_t)3 * h->na;
         TRY(to_device(h, h->A.X, x, na3 * sizeof(double), on_device));
@@ -1033,6 +1042,8 @@ lbmd_status lbmd_set_reinterpolation(lbmd_t h, int on) {
     if (!h) return fail(nullptr, LBMD_ERR_ARG, "handle is NULL");
     if (on != 0 && on != 1) return fail(h, LBMD_ERR_ARG, "on must be 0 or 1");
     if (on && h->na == 0) return fail(h, LBMD_ERR_ARG, "re-interpolation needs atoms (n_atoms > 0)");
+    if (on && h->p.deterministic)
+        return fail(h, LBMD_ERR_ARG, "the deterministic mode covers the frozen-velocity coupling only");
     AtomArgs &A = h->A;
     CouplingArgs &C = h->C;
     if (on) {
@@ -1120,6 +1131,8 @@ lbmd_status backward_impl(lbmd_t h, int n_steps, int ckpt_every, int observable,
         return fail(h, LBMD_ERR_ARG, "the adjoint differentiates the deterministic step: set kT = 0 (lbmd_set_thermal)");
     if (h->A.reinterp)
         return fail(h, LBMD_ERR_ARG, "the adjoint covers the frozen-velocity coupling: turn re-interpolation off");
+    if (h->p.deterministic)
+        return fail(h, LBMD_ERR_ARG, "the adjoint runs with deterministic = 0 (its reverse sums use float atomics)");
     TRY(adj_prepare(h, n_steps, ckpt_every));
     cudaStream_t s = h->stream;
     const int K = ckpt_every, nseg = (n_steps + K - 1) / K;

@@ -90,6 +90,7 @@ struct AtomArgs {
     int *tag, *touched;      // touched-node stamps and list (as the interpolation's)
     int touched_cap;
     float half_skin2;     // (skin/2)^2, drift that triggers a rebuild
+    int det;              // deterministic mode: lists sorted by atom index, set-up forces in fixed point
     int *scan_local;      // Morton-code exclusive scan within blocks of 1024
     int *scan_block;      // kMortonCodes / 1024 block offsets
     DevState *ds;
@@ -133,7 +134,13 @@ struct CouplingArgs {
     float4 *unode;     // node velocities of the step's region (re-interpolation only)
     DevState *ds;
     int keep;       // 1: the fix-up leaves G and the touched list for the adjoint
+    // Deterministic mode: the spread adds fixed-point integers (exact, so
+    // independent of the order of the atomics) per touched slot instead of
+    // float4 atomics per node; tslot maps a node to its touched slot.
+    int *tslot;
+    long long *gfix;  // 3 per touched slot, in units of 1/kFixScale
 };
+constexpr double kFixScale = 1099511627776.0;  // 2^40: fixed-point unit of the deterministic spread
 
 // Adjoint state and accumulators of lbmd_backward.
 struct AdjArgs {

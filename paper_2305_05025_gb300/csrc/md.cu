@@ -193,6 +193,10 @@ __device__ void md_force_warp(const AtomArgs &A, const float4 *__restrict__ P, c
     }
     const int total = A.bwin == 5 ? cell_table<5>(A, g3, cc, t, A.rc2f, tab) : cell_table<3>(A, g3, cc, t, A.rc2f, tab);
     float fx = 0.f, fy = 0.f, fz = 0.f;
+    // Deterministic mode: each pair force also enters an exact fixed-point
+    // sum (2^-32 units), independent of the candidates' order in the buckets.
+    long long qx = 0, qy = 0, qz = 0;
+    const double qs = 4294967296.0;
     for (int t0 = lane; t0 < total; t0 += 32) {
         int before;
         const int pos = cand_cell(tab, t0, before);
@@ -210,9 +214,27 @@ __device__ void md_force_warp(const AtomArgs &A, const float4 *__restrict__ P, c
         float fr = A.lj_24eps * inv_r2 * sr6 * (2.f * sr6 - 1.f) - A.lj_fc * rsqrtf(r2);
         if (A.coul && r2 < A.coul_rc2)
             fr += A.coul_2c * pa.w * P[q].w * (inv_r2 * inv_r2 - A.coul_irc3 * rsqrtf(r2));
-        fx += fr * d[0];
-        fy += fr * d[1];
-        fz += fr * d[2];
+        if (A.det) {
+            qx += llrint((double)(fr * d[0]) * qs);
+            qy += llrint((double)(fr * d[1]) * qs);
+            qz += llrint((double)(fr * d[2]) * qs);
+        } else {
+            fx += fr * d[0];
+            fy += fr * d[1];
+            fz += fr * d[2];
+        }
+    }
+    if (A.det) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            qx += __shfl_xor_sync(0xffffffffu, qx, o);
+            qy += __shfl_xor_sync(0xffffffffu, qy, o);
+            qz += __shfl_xor_sync(0xffffffffu, qz, o);
+        }
+        // every lane holds the exact sum: lane 0 carries it, the others none
+        fx = lane == 0 ? (float)((double)qx / qs) : 0.f;
+        fy = lane == 0 ? (float)((double)qy / qs) : 0.f;
+        fz = lane == 0 ? (float)((double)qz / qs) : 0.f;
     }
     for (int sb = A.bstart[a] + lane; sb < A.bstart[a + 1]; sb += 32) {
         const int q = A.bpart[sb];
@@ -397,13 +419,38 @@ __global__ void k_prime_force(AtomArgs A) {
 // the buckets of that generation, inside the same kernel. Flags rotate over
 // three slots like the buckets: kernel k reads slot g, raises g+1, clears g-1.
 
+// Deterministic mode: a list in ascending atom index (the bucket slots fill
+// in the order of atomics), so the force sums in the same order every run.
+// A bitonic sort of 256 entries by the warp in its 256-int scratch row; out
+// of line, so the rare path keeps its registers to itself.
+__device__ __noinline__ void sort_list(int *out, int n, int *tab) {
+    const int lane = threadIdx.x & 31;
+    __syncwarp();
+    for (int i = lane; i < 256; i += 32) tab[i] = i < n ? out[i] : 0x7fffffff;
+    __syncwarp();
+    for (int size = 2; size <= 256; size <<= 1)
+        for (int stride = size >> 1; stride > 0; stride >>= 1) {
+            for (int i = lane; i < 128; i += 32) {
+                const int lo = 2 * stride * (i / stride) + (i % stride), hi = lo + stride;
+                const int x = tab[lo], y = tab[hi];
+                if ((x > y) == ((lo & size) == 0)) {
+                    tab[lo] = y;
+                    tab[hi] = x;
+                }
+            }
+            __syncwarp();
+        }
+    for (int i = lane; i < n; i += 32) out[i] = tab[i];
+    __syncwarp();
+}
+
 // Builds atom a's list with the warp: candidates of the MD cells within the
 // list radius (cell_table), NBB per lane per round (all
 // their slot loads issued together, then all their position loads, so a
 // round costs two dependent memory latencies), ballot compaction. Bonded
 // partners (the first 32) sit one per lane and are matched with shuffles,
 // without touching memory per candidate.
-template <int NBB, int W>
+template <int NBB, int W, bool DET>
 __device__ __noinline__ void build_list(const AtomArgs &A, const float4 *__restrict__ P,
                                         const float4 *__restrict__ Lq, int g3, int a, float4 pa, float4 la, int b0,
                                         int b1) {
@@ -495,6 +542,7 @@ __device__ __noinline__ void build_list(const AtomArgs &A, const float4 *__restr
             kept += __popc(m);
         }
     }
+    if constexpr (DET) sort_list(out, min(kept, NL_MAX), tab);
     if (lane == 0) {
         A.nnb[a] = min(kept, NL_MAX);
         if (kept > NL_MAX) atomicOr(&A.ds->flags, FLAG_CELL);
@@ -639,7 +687,7 @@ __device__ __forceinline__ float far_velocity(const void *src, int store, const 
 // 20k-atom grid fits one wave); 4 lanes at 10 blocks (48 registers): 8%
 // faster than 8 blocks at 64 registers on 200k atoms, where the grid takes
 // several waves and more resident warps hide more latency.
-template <int TPA, int NB, int W, bool RI>
+template <int TPA, int NB, int W, bool RI, bool DET>
 __global__ void __launch_bounds__(128, TPA == 8 ? 9 : 10) k_md_substep(AtomArgs A, int k) {
     const int lane = threadIdx.x & 31;
     const int sub = lane & (TPA - 1);
@@ -702,7 +750,7 @@ __global__ void __launch_bounds__(128, TPA == 8 ? 9 : 10) k_md_substep(AtomArgs 
                 const int bg0 = __shfl_sync(0xffffffffu, b0, g * TPA), bg1 = __shfl_sync(0xffffffffu, b1, g * TPA);
                 const float4 pg = shfl4(pa, g * TPA);
                 const float4 lg = shfl4(la, g * TPA);
-                if (vg) build_list<NBB, W>(A, A.P[par], A.L[par], g3, ag, pg, lg, bg0, bg1);
+                if (vg) build_list<NBB, W, DET>(A, A.P[par], A.L[par], g3, ag, pg, lg, bg0, bg1);
             }
             __syncwarp();
             nlist = A.nnb[a];
@@ -938,7 +986,7 @@ cudaError_t launch_md_prime(const AtomArgs &a, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-template <int TPA, int W, bool RI>
+template <int TPA, int W, bool RI, bool DET>
 cudaError_t launch_substep(const AtomArgs &a, int k, cudaStream_t s) {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((a.na + 4 * (32 / TPA) - 1) / (4 * (32 / TPA)));  // 128 threads, TPA lanes per atom
@@ -949,7 +997,7 @@ cudaError_t launch_substep(const AtomArgs &a, int k, cudaStream_t s) {
     attr[0].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, k_md_substep<TPA, 2, W, RI>, a, k);
+    return cudaLaunchKernelEx(&cfg, k_md_substep<TPA, 2, W, RI, DET>, a, k);
 }
 
 cudaError_t launch_md_substep(const AtomArgs &a, int k, cudaStream_t s) {
@@ -957,11 +1005,19 @@ cudaError_t launch_md_substep(const AtomArgs &a, int k, cudaStream_t s) {
     // Above ~64k atoms the 8-lane grid no longer fits the GPU in one wave.
     if (a.reinterp) {
         if (a.bwin == 5)
-            return a.na > 65536 ? launch_substep<4, 5, true>(a, k, s) : launch_substep<8, 5, true>(a, k, s);
-        return a.na > 65536 ? launch_substep<4, 3, true>(a, k, s) : launch_substep<8, 3, true>(a, k, s);
+            return a.na > 65536 ? launch_substep<4, 5, true, false>(a, k, s) : launch_substep<8, 5, true, false>(a, k, s);
+        return a.na > 65536 ? launch_substep<4, 3, true, false>(a, k, s) : launch_substep<8, 3, true, false>(a, k, s);
     }
-    if (a.bwin == 5) return a.na > 65536 ? launch_substep<4, 5, false>(a, k, s) : launch_substep<8, 5, false>(a, k, s);
-    return a.na > 65536 ? launch_substep<4, 3, false>(a, k, s) : launch_substep<8, 3, false>(a, k, s);
+    // Deterministic mode (sorted lists) in its own instantiations: the
+    // default ones carry none of its code. It excludes re-interpolation.
+    if (a.det) {
+        if (a.bwin == 5)
+            return a.na > 65536 ? launch_substep<4, 5, false, true>(a, k, s) : launch_substep<8, 5, false, true>(a, k, s);
+        return a.na > 65536 ? launch_substep<4, 3, false, true>(a, k, s) : launch_substep<8, 3, false, true>(a, k, s);
+    }
+    if (a.bwin == 5)
+        return a.na > 65536 ? launch_substep<4, 5, false, false>(a, k, s) : launch_substep<8, 5, false, false>(a, k, s);
+    return a.na > 65536 ? launch_substep<4, 3, false, false>(a, k, s) : launch_substep<8, 3, false, false>(a, k, s);
 }
 
 cudaError_t launch_md_sort(const AtomArgs &a, cudaStream_t s) {

@@ -53,7 +53,7 @@ def params_from(cfg):
                        float(cfg.get("force_amp", 0.0)), int(cfg.get("force_dir", 0)),
                        int(cfg.get("force_wave_axis", 1)), int(cfg.get("walls_z", 0)),
                        STORES[store] if isinstance(store, str) else int(store),
-                       0, int(cfg.get("check_every", 0)))
+                       int(cfg.get("deterministic", 0)), int(cfg.get("check_every", 0)))
 
 
 _lib = None

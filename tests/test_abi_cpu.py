@@ -75,7 +75,7 @@ def _create(params, **kw):
     (dict(store=7), "store"),
     (dict(forcing=9), "forcing"),
     (dict(walls_z=1, nz=1), "walls"),
-    (dict(deterministic=1), "deterministic"),
+    (dict(deterministic=2), "deterministic"),
     (dict(force_dir=3), "force_dir"),
 ])
 def test_invalid_params_are_rejected_before_device_work(L, change, msg):
