@@ -24,16 +24,21 @@ def test_reference_arm_prints_the_contract_line():
     assert line["e2e"] == {"value": line["value"], "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
 
 
-def test_traffic_records_are_tied_to_their_kernel_sources():
+def test_traffic_records_are_tied_to_their_kernel_sources(tmp_path, monkeypatch):
     """The DRAM traffic bench.py reports comes from profiles/*.json only while
-    the hash of the kernel's sources matches the recorded one: the committed
-    records match the committed sources, and any other source set (a changed
-    kernel) yields no figure."""
+    the hash of the kernel's sources matches the recorded one: a record taken
+    on one source is returned, and nothing once that source changes."""
     sys.path.insert(0, ROOT)
     import bench
 
-    assert bench._traffic("f16", 512 ** 3) is not None
-    assert bench._traffic("f32", 512 ** 3) is not None
-    assert bench._md_traffic(200000) is not None
-    assert bench._recorded("lb_step_traffic.json", "f16", ("lb_step.cu",)) is None
-    assert bench._recorded("md_substep_traffic.json", "k_md_substep", ("md.cu",)) is None
+    csrc = tmp_path / "paper_2305_05025_gb300" / "csrc"
+    csrc.mkdir(parents=True)
+    (tmp_path / "profiles").mkdir()
+    (csrc / "k.cu").write_text("// kernel, first version\n")
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    rec = {"f16": {"kernel_hash": bench._kernel_hash(("k.cu",)), "dram_bytes_per_node": 72.7}}
+    (tmp_path / "profiles" / "t.json").write_text(json.dumps(rec))
+    assert bench._recorded("t.json", "f16", ("k.cu",))["dram_bytes_per_node"] == 72.7
+    (csrc / "k.cu").write_text("// kernel, changed\n")
+    assert bench._recorded("t.json", "f16", ("k.cu",)) is None
+    assert bench._recorded("t.json", "f32", ("k.cu",)) is None
